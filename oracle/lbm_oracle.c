@@ -329,6 +329,12 @@ static double sigma_of(const oracle_t *o, double T)
     return o->p.sigma0 + o->p.sigma1 * d + o->p.sigma2 * d * d;
 }
 
+static double dsigma_of(const oracle_t *o, double T)   /* sigma(T) - sigma0 */
+{
+    double d = T - o->p.T_ref;
+    return o->p.sigma1 * d + o->p.sigma2 * d * d;
+}
+
 void or_destroy(void *handle);
 
 void *or_create(const or_params *prm)
@@ -587,7 +593,9 @@ static void step_once(oracle_t *o)
             if (j < 0) T = 2.0 * T_bottom(o, (double)i) - o->T[FLD(0, i)];
             else if (j >= ny) T = 2.0 * o->p.T_cold - o->T[FLD(ny - 1, i)];
             else T = o->T[FLD(j, i)];
-            o->sig[EXT(j, i)] = sigma_of(o, T);
+            /* grad(sigma) = grad(sigma - sigma0): the constant is left out of the
+             * differences, where it would only add round-off. */
+            o->sig[EXT(j, i)] = dsigma_of(o, T);
             int js = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
             double ph = o->phix[EXT(j, i)];
             o->psi[EXT(j, i)] = o->dp_prev[FLD(js, i)] - rho_of(o, ph) * CS2;
