@@ -1,0 +1,154 @@
+/*
+ * lbm_gb300.h -- C ABI of the GB300 (sm_103a) coupled central-moment lattice Boltzmann
+ * stepper for thermocapillary convection in superimposed fluid layers (arXiv 2210.07501).
+ *
+ * One time step advances three lattices at every node of an nx x ny channel:
+ *   - the conservative Allen-Cahn phase field phi (Sec. 4.1; D2Q5 or D2Q9),
+ *   - the two-fluid pressure/velocity lattice with the CSF surface-tension and Marangoni
+ *     force (Sec. 4.2; D2Q9),
+ *   - the energy lattice for T (Sec. 4.3; D2Q5 or D2Q9),
+ * each collided in central-moment space through the maps P, F(u), F(-u), P^-1 of App. B
+ * and streamed by a pull scheme, with sigma(T) = sigma0 + sigma1 (T - T_ref)
+ * + sigma2 (T - T_ref)^2 (Sec. 2.3).
+ *
+ * Geometry (Sec. 2.1): periodic in x; walls at y = 0 (heated, T = T_hot + dT cos(2 pi k x /
+ * nx)) and y = ny (T = T_cold), halfway between node rows; node (i, j) sits at x = i,
+ * y = j + 1/2.  Flow walls are no-slip (bounce-back), the phase field has no flux through
+ * the wall (specular reflection), temperature walls are Dirichlet (anti-bounce-back),
+ * Sec. 5.1.  Fluid A (phi = 0) fills the bottom layer y < b, fluid B (phi = 1) the top.
+ *
+ * Conventions shared by every entry point:
+ *   - Field arrays are row-major [ny][nx] doubles; row j = 0 is next to the heated wall,
+ *     column i = 0 is under the heating peak.
+ *   - Populations exchanged with the caller are [Q][ny][nx] doubles in the variables the
+ *     solver carries: f (phase field), g - w_a p0 (flow, p0 = rho_bottom / 3) and
+ *     h - w_a T_ref (energy); "dp" is p - p0.
+ *   - Every function returns LBM_OK (0) or a negative LBM_E* status and never throws.
+ *     A handle is not thread-safe: use one handle per host thread.
+ *   - The library owns all device memory it allocates; the caller owns every buffer it
+ *     passes in.  Host pointers may be pageable or pinned.
+ *   - Work is queued on the handle's CUDA stream; functions that return data to host
+ *     memory synchronise that stream before returning.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* bad argument, size or parameter                       */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed                       */
+#define LBM_ECUDA (-3)     /* a CUDA call failed; lbm_strerror names it              */
+#define LBM_EUNSTABLE (-4) /* a non-finite value appeared in the macroscopic fields  */
+#define LBM_ETIMEOUT (-5)  /* run_to_steady reached max_steps before the tolerance   */
+#define LBM_EIO (-6)       /* checkpoint file could not be read or written, or is bad */
+
+/* ---- storage precision of the populations (arithmetic: FP64 for LBM_FP64, else FP32) ---- */
+#define LBM_FP64 0
+#define LBM_FP32 1
+#define LBM_FP16 2
+
+/* ---- dtype of device field exports ---- */
+#define LBM_DTYPE_F64 0
+#define LBM_DTYPE_F32 1
+
+typedef struct lbm_handle lbm_handle;
+
+/* Lattice and discretisation (Sec. 2.1, Sec. 4). */
+typedef struct {
+    int32_t nx, ny;        /* nodes; nx >= 3, ny >= 3, nx * ny <= 2^31                    */
+    int32_t heat_periods;  /* cosine periods of the bottom-wall temperature along x (>= 0) */
+    int32_t q_phi;         /* 5 or 9: phase-field lattice                                  */
+    int32_t q_T;           /* 5 or 9: energy lattice                                       */
+    int32_t precision;     /* LBM_FP64 | LBM_FP32 | LBM_FP16                                */
+    double b;              /* height of the interface above the bottom wall (0 < b < ny)   */
+    double W;              /* interface width (> 0)                                        */
+} lbm_domain;
+
+/* Fluid and thermal parameters (Sec. 2.2, 2.3, 3, 4). Lattice units. */
+typedef struct {
+    double sigma0, sigma1, sigma2;   /* sigma(T) = sigma0 + sigma1 (T-T_ref) + sigma2 (T-T_ref)^2 */
+    double T_ref;                    /* reference temperature; also the initial T          */
+    double T_hot, T_cold, dT;        /* bottom wall T_hot + dT cos(..), top wall T_cold     */
+    double tau_flow;                 /* bottom fluid: nu = (tau_flow - 1/2) / 3  (> 1/2)    */
+    double visc_ratio;               /* mu_top / mu_bottom (> 0)                            */
+    double tau_T;                    /* bottom fluid: alpha = (tau_T - 1/2) / 3  (> 1/2)    */
+    double cond_ratio;               /* k_top / k_bottom (> 0)                              */
+    double tau_phi;                  /* mobility M_phi = (tau_phi - 1/2) / 3  (> 1/2)       */
+    double rho_bottom, rho_top;      /* densities (> 0); c_p = 1                            */
+    double Fx_ext, Fy_ext;           /* uniform external body force F_ext                   */
+} lbm_params;
+
+/* Create a solver, allocate its device state and initialise it at rest: tanh interface of
+ * width W at y = b (Sec. 3), u = 0, T = T_ref, uniform pressure p0.  `stream` is a
+ * cudaStream_t to queue work on (NULL: the library creates its own).  *out receives the
+ * handle (NULL on failure).  Uses the current CUDA device. */
+int lbm_create(const lbm_domain *domain, const lbm_params *params, void *stream, lbm_handle **out);
+
+/* Re-initialise at the central-moment equilibrium of the given host fields [ny][nx]
+ * (phi, u, v, T, dp = p - p0); a NULL field takes its default from lbm_create.  Resets
+ * the step counter. */
+int lbm_init_fields(lbm_handle *h, const double *phi, const double *u, const double *v,
+                    const double *T, const double *dp);
+
+/* Queue nsteps >= 0 time steps (Sec. 4.1-4.3: stream, moments, stencils, forces, collide).
+ * Asynchronous; returns LBM_EINVAL / LBM_ECUDA only for launch-time errors.  Every
+ * check_interval steps the macroscopic fields are stored and reduced (mass, residual). */
+int lbm_step(lbm_handle *h, int64_t nsteps);
+
+/* Macroscopic fields of the latest step (the values its collision used): phi, u, v, T and
+ * p - p0, into caller-owned host arrays [ny][nx]; any pointer may be NULL.  Synchronises. */
+int lbm_fields(lbm_handle *h, double *phi, double *u, double *v, double *T, double *dp);
+
+/* As lbm_fields, into caller-owned device arrays [ny][nx] of LBM_DTYPE_F64 or
+ * LBM_DTYPE_F32 (e.g. torch tensors).  Asynchronous on the handle's stream. */
+int lbm_fields_device(lbm_handle *h, void *phi, void *u, void *v, void *T, void *dp, int dtype);
+
+/* Global diagnostics (spec reductions, FP64 accumulation in a fixed order):
+ * mass = sum of phi over the lattice at the current step; residual = ||u^n - u^{n-K}||_2 /
+ * (K ||u^n||_2) over both components from the last two checks K steps apart (-1 before
+ * two checks); step = steps taken.  Returns LBM_EUNSTABLE if a non-finite value was seen.
+ * Synchronises. */
+int lbm_diag(lbm_handle *h, double *mass, double *residual, int64_t *step);
+
+/* Steps every check_interval (K >= 1) steps between residual checks; default 100. */
+int lbm_set_check_interval(lbm_handle *h, int32_t K);
+
+/* Step until residual <= tol or max_steps are taken; *steps_taken (may be NULL) receives
+ * the count.  Returns LBM_OK, LBM_ETIMEOUT, LBM_EUNSTABLE or an error. Synchronises. */
+int lbm_run_to_steady(lbm_handle *h, double tol, int64_t max_steps, int64_t *steps_taken);
+
+/* Post-collision state in solver variables (see conventions): f [q_phi][ny][nx],
+ * g [9][ny][nx], h [q_T][ny][nx], dp [ny][nx] (pressure used by the next step's force). */
+int lbm_get_state(lbm_handle *h, double *f, double *g, double *hT, double *dp);
+int lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *hT, const double *dp);
+
+/* Checkpoint: the raw device state, step counter, domain, parameters and a CRC32 of the
+ * payload.  lbm_load requires a file written for the same domain and precision and
+ * restores the state bit for bit.  LBM_EIO on a missing, truncated or corrupt file. */
+int lbm_save(lbm_handle *h, const char *path);
+int lbm_load(lbm_handle *h, const char *path);
+
+/* Bytes the step kernel moves per lattice node and step (populations read and written
+ * once plus the stored pressure), for roofline accounting. */
+int lbm_bytes_per_node(const lbm_handle *h, int64_t *bytes);
+
+/* Number of step-kernel launches queued since creation (diagnostics). */
+int lbm_launch_count(const lbm_handle *h, int64_t *launches);
+
+/* Release the handle and its device memory; NULL-safe. */
+void lbm_destroy(lbm_handle *h);
+
+/* Static string for a status code (for LBM_ECUDA, of the last CUDA error seen). */
+const char *lbm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -470,6 +470,7 @@ int or_init(void *handle, const double *phi_in, const double *u_in, const double
     oracle_t *o = (oracle_t *)handle;
     if (!o) return -1;
     int nx = o->nx, ny = o->ny;
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = FLD(j, i);
@@ -482,6 +483,7 @@ int or_init(void *handle, const double *phi_in, const double *u_in, const double
         }
     fill_phi_ext(o, o->phi);
     normals(o);
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = FLD(j, i);
@@ -576,6 +578,7 @@ static void step_once(oracle_t *o)
     int nx = o->nx, ny = o->ny;
     stream(o);
     /* phi = sum f, T = sum h (Sec. 4.1, 4.3) */
+    #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double s = 0.0, t = 0.0;
@@ -587,6 +590,7 @@ static void step_once(oracle_t *o)
     /* stencil fields */
     fill_phi_ext(o, o->phi);
     normals(o);
+    #pragma omp parallel for schedule(static)
     for (int j = -1; j < ny + 1; ++j)
         for (int i = 0; i < nx; ++i) {
             double T;

@@ -1,0 +1,647 @@
+// lbm_api.cu -- host implementation of the C ABI declared in include/lbm_gb300.h.
+//
+// The handle owns two ping-pong copies of every population plane and of the stored
+// pressure, the bottom-wall temperature table, the macroscopic field buffer written by
+// the last step of each lbm_step call (and at every residual check), the previous
+// velocity for the residual, and the reduction scratch.  All work is queued on one CUDA
+// stream; only the entry points that return data to the host synchronise it.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/lbm_gb300.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_handle {
+    lbm_domain dom;
+    lbm_params prm;
+    int prec, Qf, Qt, nx, ny, pitch;
+    long long plane;        // ny * pitch
+    size_t esize;           // bytes per stored population value
+    size_t rsize;           // bytes per Real (pressure plane)
+    cudaStream_t stream;
+    bool own_stream;
+    void *pop[2][3];        // [buffer][f, g, h]
+    void *dp[2];
+    void *twall;            // Real [3][nx]
+    double *macro;          // [5][ny][nx]
+    double *uprev;          // [2][ny][nx]
+    double *partials;       // reduction scratch [nblk][4]
+    double *result;         // [2][4]: last check, last diag
+    double *host_result;    // pinned [8]
+    double *staging;        // lazily allocated [9][ny][nx] doubles for state I/O
+    int cur;
+    int64_t step, check_interval, launches;
+    int64_t last_check_step, prev_check_step;
+    bool have_check, have_prev_check;
+    double res_du2, res_u2;
+    double sf, sg, sh;
+    Phys<double> P;
+};
+
+static thread_local char g_errbuf[256] = "";
+
+static int cuda_fail(cudaError_t e, const char *what)
+{
+    snprintf(g_errbuf, sizeof(g_errbuf), "%s: %s", what, cudaGetErrorString(e));
+    return LBM_ECUDA;
+}
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+template <typename Real> static Phys<Real> cast_phys(const Phys<double> &d)
+{
+    Phys<Real> p;
+    p.W4 = Real(d.W4);
+    p.csf = Real(d.csf);
+    p.sigma0 = Real(d.sigma0);
+    p.sigma1 = Real(d.sigma1);
+    p.sigma2 = Real(d.sigma2);
+    p.T_ref = Real(d.T_ref);
+    p.dTcold = Real(d.dTcold);
+    p.rhoA = Real(d.rhoA);
+    p.drho = Real(d.drho);
+    p.muA = Real(d.muA);
+    p.dmu = Real(d.dmu);
+    p.kA = Real(d.kA);
+    p.dk = Real(d.dk);
+    p.omega_phi = Real(d.omega_phi);
+    p.Mphi = Real(d.Mphi);
+    p.Fx = Real(d.Fx);
+    p.Fy = Real(d.Fy);
+    p.g2min = std::is_same<Real, double>::value ? Real(1e-24) : Real(1e-20);
+    return p;
+}
+
+template <typename Real, typename Store> static StepArgs<Real, Store> make_args(const lbm_handle *h, int src, double *macro)
+{
+    StepArgs<Real, Store> A;
+    A.nx = h->nx;
+    A.ny = h->ny;
+    A.pitch = h->pitch;
+    A.plane = h->plane;
+    const int dst = 1 - src;
+    A.f_in = (const Store *)h->pop[src][0];
+    A.g_in = (const Store *)h->pop[src][1];
+    A.h_in = (const Store *)h->pop[src][2];
+    A.f_out = (Store *)h->pop[dst][0];
+    A.g_out = (Store *)h->pop[dst][1];
+    A.h_out = (Store *)h->pop[dst][2];
+    A.dp_in = (const Real *)h->dp[src];
+    A.dp_out = (Real *)h->dp[dst];
+    A.twall = (const Real *)h->twall;
+    A.macro = macro;
+    A.P = cast_phys<Real>(h->P);
+    A.sf = Real(h->sf);
+    A.sg = Real(h->sg);
+    A.sh = Real(h->sh);
+    A.isf = Real(1.0 / h->sf);
+    A.isg = Real(1.0 / h->sg);
+    A.ish = Real(1.0 / h->sh);
+    return A;
+}
+
+// Dispatch a functor templated on <Real, Store, QF, QT> for the handle's configuration.
+template <template <typename, typename, int, int> class Fn, typename... Args>
+static cudaError_t dispatch(const lbm_handle *h, Args... args)
+{
+#define LBM_CASE(PREC, R, S)                                                          \
+    if (h->prec == PREC) {                                                            \
+        if (h->Qf == 5 && h->Qt == 5) return Fn<R, S, 5, 5>::run(h, args...);         \
+        if (h->Qf == 5 && h->Qt == 9) return Fn<R, S, 5, 9>::run(h, args...);         \
+        if (h->Qf == 9 && h->Qt == 5) return Fn<R, S, 9, 5>::run(h, args...);         \
+        return Fn<R, S, 9, 9>::run(h, args...);                                       \
+    }
+    LBM_CASE(LBM_FP64, double, double)
+    LBM_CASE(LBM_FP32, float, float)
+    LBM_CASE(LBM_FP16, float, __half)
+#undef LBM_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <typename R, typename S, int QF, int QT> struct StepFn {
+    static cudaError_t run(const lbm_handle *h, int src, double *macro)
+    {
+        return launch_step<R, S, QF, QT>(make_args<R, S>(h, src, macro), h->stream);
+    }
+};
+template <typename R, typename S, int QF, int QT> struct InitFn {
+    static cudaError_t run(const lbm_handle *h, int dst, int defaults)
+    {
+        // init writes buffer `dst`: build args whose outputs are dst (inputs unused)
+        StepArgs<R, S> A = make_args<R, S>(h, 1 - dst, h->macro);
+        return launch_init<R, S, QF, QT>(A, h->dom.b, h->dom.W, defaults, h->stream);
+    }
+};
+
+static size_t store_size(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
+static size_t real_size(int prec) { return prec == LBM_FP64 ? 8 : 4; }
+
+static void free_all(lbm_handle *h)
+{
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 3; ++k)
+            if (h->pop[b][k]) cudaFree(h->pop[b][k]);
+        if (h->dp[b]) cudaFree(h->dp[b]);
+    }
+    if (h->twall) cudaFree(h->twall);
+    if (h->macro) cudaFree(h->macro);
+    if (h->uprev) cudaFree(h->uprev);
+    if (h->partials) cudaFree(h->partials);
+    if (h->result) cudaFree(h->result);
+    if (h->staging) cudaFree(h->staging);
+    if (h->host_result) cudaFreeHost(h->host_result);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+static int validate(const lbm_domain *d, const lbm_params *p)
+{
+    if (!d || !p) return LBM_EINVAL;
+    if (d->nx < 3 || d->ny < 3 || (long long)d->nx * d->ny > (1LL << 31)) return LBM_EINVAL;
+    if ((d->q_phi != 5 && d->q_phi != 9) || (d->q_T != 5 && d->q_T != 9)) return LBM_EINVAL;
+    if (d->precision < LBM_FP64 || d->precision > LBM_FP16 || d->heat_periods < 0) return LBM_EINVAL;
+    if (!(d->W > 0.0) || !(d->b > 0.0) || !(d->b < d->ny)) return LBM_EINVAL;
+    if (!(p->tau_flow > 0.5) || !(p->tau_T > 0.5) || !(p->tau_phi > 0.5)) return LBM_EINVAL;
+    if (!(p->visc_ratio > 0.0) || !(p->cond_ratio > 0.0) || !(p->rho_bottom > 0.0) || !(p->rho_top > 0.0))
+        return LBM_EINVAL;
+    const double vals[] = {p->sigma0, p->sigma1, p->sigma2, p->T_ref, p->T_hot, p->T_cold, p->dT, p->Fx_ext, p->Fy_ext};
+    for (double v : vals)
+        if (!isfinite(v)) return LBM_EINVAL;
+    return LBM_OK;
+}
+
+// Storage scale of the FP16 flow populations: g - w p0 carries w (dp + 3 rho c^2 e.u);
+// scale the expected thermocapillary velocity (Marangoni stress balance, App. C) and the
+// body-force velocity to O(0.1) so that they sit in FP16's normal range.
+static double fp16_flow_scale(const lbm_domain *d, const lbm_params *p, double muA)
+{
+    const double dsig = fabs(p->sigma1) + 2.0 * fabs(p->sigma2) * (fabs(p->dT) + fabs(p->T_hot - p->T_ref));
+    double u = dsig * fabs(p->dT) / muA * 0.25;
+    u += (fabs(p->Fx_ext) + fabs(p->Fy_ext)) * (double)d->ny * d->ny / (8.0 * muA);
+    u += fabs(p->sigma0) / (muA * (double)d->W) * 1e-3;
+    if (!(u > 1e-12)) u = 1e-12;
+    double s = exp2(floor(log2(0.05 / u)));
+    if (s < 1.0) s = 1.0;
+    if (s > 1073741824.0) s = 1073741824.0;
+    return s;
+}
+
+extern "C" {
+
+const char *lbm_strerror(int status)
+{
+    switch (status) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return g_errbuf[0] ? g_errbuf : "CUDA error";
+    case LBM_EUNSTABLE: return "non-finite value in the fields (unstable)";
+    case LBM_ETIMEOUT: return "tolerance not reached within max_steps";
+    case LBM_EIO: return "checkpoint I/O error";
+    default: return "unknown status";
+    }
+}
+
+static int reset_diag(lbm_handle *h)
+{
+    h->have_check = h->have_prev_check = false;
+    h->last_check_step = h->prev_check_step = -1;
+    h->res_du2 = h->res_u2 = 0.0;
+    const size_t N = (size_t)h->nx * h->ny;
+    CK(cudaMemsetAsync(h->uprev, 0, 2 * N * sizeof(double), h->stream));
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_domain *domain, const lbm_params *params, void *stream, lbm_handle **out)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    int rc = validate(domain, params);
+    if (rc) return rc;
+    lbm_handle *h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ENOMEM;
+    h->dom = *domain;
+    h->prm = *params;
+    h->prec = domain->precision;
+    h->Qf = domain->q_phi;
+    h->Qt = domain->q_T;
+    h->nx = domain->nx;
+    h->ny = domain->ny;
+    h->pitch = (domain->nx + 63) / 64 * 64;
+    h->plane = (long long)h->ny * h->pitch;
+    h->esize = store_size(h->prec);
+    h->rsize = real_size(h->prec);
+    h->check_interval = 100;
+    cudaError_t e;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaStreamCreate"); }
+        h->own_stream = true;
+    }
+    const int Q[3] = {h->Qf, 9, h->Qt};
+    const size_t N = (size_t)h->nx * h->ny;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        for (int k = 0; k < 3 && ok; ++k)
+            ok = cudaMalloc(&h->pop[b][k], (size_t)Q[k] * h->plane * h->esize) == cudaSuccess;
+        ok = ok && cudaMalloc(&h->dp[b], (size_t)h->plane * h->rsize) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&h->twall, 3 * (size_t)h->nx * h->rsize) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->macro, 5 * N * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->uprev, 2 * N * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->partials, (size_t)reduce_blocks() * 4 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->result, 8 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&h->host_result, 8 * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return LBM_ENOMEM;
+    }
+    // padding columns are never read, but keep them defined
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 3; ++k) cudaMemsetAsync(h->pop[b][k], 0, (size_t)Q[k] * h->plane * h->esize, h->stream);
+        cudaMemsetAsync(h->dp[b], 0, (size_t)h->plane * h->rsize, h->stream);
+    }
+    // physical constants (Sec. 2-4), lattice units, c^2 = 1/3, c_p = 1
+    const lbm_params *p = params;
+    Phys<double> &P = h->P;
+    P.W4 = 4.0 / domain->W;
+    P.csf = 1.5 * domain->W;
+    P.sigma0 = p->sigma0;
+    P.sigma1 = p->sigma1;
+    P.sigma2 = p->sigma2;
+    P.T_ref = p->T_ref;
+    P.dTcold = p->T_cold - p->T_ref;
+    P.rhoA = p->rho_bottom;
+    P.drho = p->rho_top - p->rho_bottom;
+    const double nuA = (p->tau_flow - 0.5) / 3.0, alphaA = (p->tau_T - 0.5) / 3.0;
+    P.muA = p->rho_bottom * nuA;
+    P.dmu = (p->visc_ratio - 1.0) * P.muA;
+    P.kA = p->rho_bottom * alphaA;
+    P.dk = (p->cond_ratio - 1.0) * P.kA;
+    P.omega_phi = 1.0 / p->tau_phi;
+    P.Mphi = (1.0 / P.omega_phi - 0.5) / 3.0;
+    P.Fx = p->Fx_ext;
+    P.Fy = p->Fy_ext;
+    P.g2min = 0.0;
+    h->sf = h->sh = 1.0;
+    h->sg = h->prec == LBM_FP16 ? fp16_flow_scale(domain, p, P.muA) : 1.0;
+    // bottom-wall temperature minus T_ref at x - 1/2, x, x + 1/2 (heating peak at x = 0)
+    {
+        double *tw = (double *)malloc(3 * (size_t)h->nx * sizeof(double));
+        if (!tw) { free_all(h); delete h; return LBM_ENOMEM; }
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < h->nx; ++i) {
+                const double x = (double)i + 0.5 * (double)(k - 1);
+                tw[k * h->nx + i] = p->T_hot + p->dT * cos(2.0 * M_PI * (double)domain->heat_periods * x / (double)h->nx) - p->T_ref;
+            }
+        cudaError_t ce;
+        if (h->rsize == 8) {
+            ce = cudaMemcpy(h->twall, tw, 3 * (size_t)h->nx * sizeof(double), cudaMemcpyHostToDevice);
+        } else {
+            float *twf = (float *)malloc(3 * (size_t)h->nx * sizeof(float));
+            if (!twf) { free(tw); free_all(h); delete h; return LBM_ENOMEM; }
+            for (int i = 0; i < 3 * h->nx; ++i) twf[i] = (float)tw[i];
+            ce = cudaMemcpy(h->twall, twf, 3 * (size_t)h->nx * sizeof(float), cudaMemcpyHostToDevice);
+            free(twf);
+        }
+        free(tw);
+        if (ce != cudaSuccess) { free_all(h); delete h; return cuda_fail(ce, "cudaMemcpy(twall)"); }
+    }
+    rc = lbm_init_fields(h, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (rc) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle *h, const double *phi, const double *u, const double *v, const double *T,
+                    const double *dp)
+{
+    if (!h) return LBM_EINVAL;
+    const size_t N = (size_t)h->nx * h->ny;
+    const double *src[5] = {phi, u, v, T, dp};
+    int defaults = 0;
+    for (int k = 0; k < 5; ++k) {
+        if (src[k]) CK(cudaMemcpyAsync(h->macro + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        else defaults |= 1 << k;
+    }
+    h->cur = 0;
+    CK(dispatch<InitFn>(h, 0, defaults));
+    h->step = 0;
+    int rc = reset_diag(h);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+static int run_check(lbm_handle *h)
+{
+    const long long N = (long long)h->nx * h->ny;
+    CK(launch_reduce(h->macro, h->uprev, N, 1, h->partials, reduce_blocks(), h->result, h->stream));
+    h->prev_check_step = h->last_check_step;
+    h->have_prev_check = h->have_check;
+    h->last_check_step = h->step;
+    h->have_check = true;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle *h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return LBM_EINVAL;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        const bool last = (s == nsteps - 1);
+        const bool check = h->check_interval > 0 && ((h->step + 1) % h->check_interval == 0);
+        double *macro = (last || check) ? h->macro : nullptr;
+        CK(dispatch<StepFn>(h, h->cur, macro));
+        h->cur = 1 - h->cur;
+        h->step += 1;
+        h->launches += 1;
+        if (check) {
+            int rc = run_check(h);
+            if (rc) return rc;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_handle *h, double *phi, double *u, double *v, double *T, double *dp)
+{
+    if (!h) return LBM_EINVAL;
+    const size_t N = (size_t)h->nx * h->ny;
+    double *dst[5] = {phi, u, v, T, dp};
+    for (int k = 0; k < 5; ++k)
+        if (dst[k]) CK(cudaMemcpyAsync(dst[k], h->macro + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_fields_device(lbm_handle *h, void *phi, void *u, void *v, void *T, void *dp, int dtype)
+{
+    if (!h || (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)) return LBM_EINVAL;
+    const long long N = (long long)h->nx * h->ny;
+    void *dst[5] = {phi, u, v, T, dp};
+    for (int k = 0; k < 5; ++k)
+        if (dst[k]) CK(launch_export(h->macro + k * N, dst[k], N, dtype == LBM_DTYPE_F32, h->stream));
+    return LBM_OK;
+}
+
+int lbm_diag(lbm_handle *h, double *mass, double *residual, int64_t *step)
+{
+    if (!h) return LBM_EINVAL;
+    const long long N = (long long)h->nx * h->ny;
+    // residual terms of the last check, then a fresh mass / finiteness reduction
+    CK(cudaMemcpyAsync(h->host_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(launch_reduce(h->macro, h->uprev, N, 0, h->partials, reduce_blocks(), h->result + 4, h->stream));
+    CK(cudaMemcpyAsync(h->host_result + 4, h->result + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double *r = h->host_result;
+    if (mass) *mass = r[4];
+    if (residual) {
+        const int64_t K = h->last_check_step - h->prev_check_step;
+        if (h->have_check && h->have_prev_check && K > 0 && r[2] > 0.0)
+            *residual = sqrt(r[1]) / ((double)K * sqrt(r[2]));
+        else
+            *residual = -1.0;
+    }
+    if (step) *step = h->step;
+    if (r[7] > 0.0 || (h->have_check && r[3] > 0.0)) return LBM_EUNSTABLE;
+    return LBM_OK;
+}
+
+int lbm_set_check_interval(lbm_handle *h, int32_t K)
+{
+    if (!h || K < 1) return LBM_EINVAL;
+    h->check_interval = K;
+    return LBM_OK;
+}
+
+int lbm_run_to_steady(lbm_handle *h, double tol, int64_t max_steps, int64_t *steps_taken)
+{
+    if (!h || !(tol > 0.0) || max_steps < 0) return LBM_EINVAL;
+    int64_t done = 0;
+    int rc = LBM_ETIMEOUT;
+    while (done < max_steps) {
+        int64_t n = h->check_interval - (h->step % h->check_interval);
+        if (n > max_steps - done) n = max_steps - done;
+        int e = lbm_step(h, n);
+        if (e) return e;
+        done += n;
+        double res;
+        e = lbm_diag(h, nullptr, &res, nullptr);
+        if (e) { rc = e; break; }
+        if (h->last_check_step == h->step && res >= 0.0 && res <= tol) { rc = LBM_OK; break; }
+    }
+    if (steps_taken) *steps_taken = done;
+    return rc;
+}
+
+}  // extern "C"
+
+template <typename R, typename S, int QF, int QT> struct GetFn {
+    static cudaError_t run(const lbm_handle *h, double *stage, int lattice, int Q, int toStore)
+    {
+        const double sc = lattice == 0 ? h->sf : (lattice == 1 ? h->sg : h->sh);
+        if (toStore) return launch_to_store<R, S>(stage, (S *)h->pop[h->cur][lattice], Q, h->nx, h->ny, h->pitch, R(sc), h->stream);
+        return launch_from_store<R, S>((const S *)h->pop[h->cur][lattice], stage, Q, h->nx, h->ny, h->pitch, R(1.0 / sc), h->stream);
+    }
+};
+template <typename R, typename S, int QF, int QT> struct DpFn {
+    static cudaError_t run(const lbm_handle *h, double *stage, int toStore)
+    {
+        if (toStore) return launch_to_store<R, R>(stage, (R *)h->dp[h->cur], 1, h->nx, h->ny, h->pitch, R(1), h->stream);
+        return launch_from_store<R, R>((const R *)h->dp[h->cur], stage, 1, h->nx, h->ny, h->pitch, R(1), h->stream);
+    }
+};
+
+extern "C" {
+
+static int ensure_staging(lbm_handle *h)
+{
+    if (h->staging) return LBM_OK;
+    const size_t N = (size_t)h->nx * h->ny;
+    if (cudaMalloc((void **)&h->staging, 9 * N * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ENOMEM;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_handle *h, double *f, double *g, double *hT, double *dp)
+{
+    if (!h || !f || !g || !hT || !dp) return LBM_EINVAL;
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    const size_t N = (size_t)h->nx * h->ny;
+    double *dst[3] = {f, g, hT};
+    const int Q[3] = {h->Qf, 9, h->Qt};
+    for (int k = 0; k < 3; ++k) {
+        CK(dispatch<GetFn>(h, h->staging, k, Q[k], 0));
+        CK(cudaMemcpyAsync(dst[k], h->staging, Q[k] * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    CK(dispatch<DpFn>(h, h->staging, 0));
+    CK(cudaMemcpyAsync(dp, h->staging, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *hT, const double *dp)
+{
+    if (!h || !f || !g || !hT || !dp) return LBM_EINVAL;
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+    const size_t N = (size_t)h->nx * h->ny;
+    const double *src[3] = {f, g, hT};
+    const int Q[3] = {h->Qf, 9, h->Qt};
+    for (int k = 0; k < 3; ++k) {
+        CK(cudaMemcpyAsync(h->staging, src[k], Q[k] * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(dispatch<GetFn>(h, h->staging, k, Q[k], 1));
+    }
+    CK(cudaMemcpyAsync(h->staging, dp, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(dispatch<DpFn>(h, h->staging, 1));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+// ---- checkpoints ----
+static uint32_t crc32_update(uint32_t crc, const unsigned char *p, size_t n)
+{
+    static uint32_t table[256];
+    static bool init = false;
+    if (!init) {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : (c >> 1);
+            table[i] = c;
+        }
+        init = true;
+    }
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+    return ~crc;
+}
+
+struct ckpt_header {
+    char magic[8];
+    uint32_t version, crc;
+    int64_t step;
+    lbm_domain dom;
+    lbm_params prm;
+    uint64_t payload;
+};
+
+static size_t state_bytes(const lbm_handle *h)
+{
+    return ((size_t)(h->Qf + 9 + h->Qt) * h->plane) * h->esize + (size_t)h->plane * h->rsize;
+}
+
+int lbm_save(lbm_handle *h, const char *path)
+{
+    if (!h || !path) return LBM_EINVAL;
+    const size_t bytes = state_bytes(h);
+    unsigned char *buf = (unsigned char *)malloc(bytes);
+    if (!buf) return LBM_ENOMEM;
+    size_t off = 0;
+    const int Q[3] = {h->Qf, 9, h->Qt};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        const size_t nb = (size_t)Q[k] * h->plane * h->esize;
+        e = cudaMemcpyAsync(buf + off, h->pop[h->cur][k], nb, cudaMemcpyDeviceToHost, h->stream);
+        off += nb;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + off, h->dp[h->cur], (size_t)h->plane * h->rsize, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { free(buf); return cuda_fail(e, "lbm_save copy"); }
+    ckpt_header hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LBMGB300", 8);
+    hd.version = 1;
+    hd.step = h->step;
+    hd.dom = h->dom;
+    hd.prm = h->prm;
+    hd.payload = bytes;
+    hd.crc = crc32_update(0, buf, bytes);
+    FILE *fp = fopen(path, "wb");
+    int rc = LBM_OK;
+    if (!fp) rc = LBM_EIO;
+    else {
+        if (fwrite(&hd, sizeof(hd), 1, fp) != 1 || fwrite(buf, 1, bytes, fp) != bytes) rc = LBM_EIO;
+        if (fclose(fp) != 0) rc = LBM_EIO;
+    }
+    free(buf);
+    return rc;
+}
+
+int lbm_load(lbm_handle *h, const char *path)
+{
+    if (!h || !path) return LBM_EINVAL;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return LBM_EIO;
+    ckpt_header hd;
+    const size_t bytes = state_bytes(h);
+    if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, "LBMGB300", 8) != 0 || hd.version != 1 ||
+        hd.payload != bytes || hd.dom.nx != h->dom.nx || hd.dom.ny != h->dom.ny || hd.dom.q_phi != h->dom.q_phi ||
+        hd.dom.q_T != h->dom.q_T || hd.dom.precision != h->dom.precision) {
+        fclose(fp);
+        return LBM_EIO;
+    }
+    unsigned char *buf = (unsigned char *)malloc(bytes);
+    if (!buf) { fclose(fp); return LBM_ENOMEM; }
+    const bool ok = fread(buf, 1, bytes, fp) == bytes;
+    fclose(fp);
+    if (!ok || crc32_update(0, buf, bytes) != hd.crc) { free(buf); return LBM_EIO; }
+    size_t off = 0;
+    const int Q[3] = {h->Qf, 9, h->Qt};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        const size_t nb = (size_t)Q[k] * h->plane * h->esize;
+        e = cudaMemcpyAsync(h->pop[h->cur][k], buf + off, nb, cudaMemcpyHostToDevice, h->stream);
+        off += nb;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dp[h->cur], buf + off, (size_t)h->plane * h->rsize, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    free(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_load copy");
+    h->step = hd.step;
+    return reset_diag(h);
+}
+
+int lbm_bytes_per_node(const lbm_handle *h, int64_t *bytes)
+{
+    if (!h || !bytes) return LBM_EINVAL;
+    *bytes = (int64_t)(2 * (h->Qf + 9 + h->Qt) * h->esize + 2 * h->rsize);
+    return LBM_OK;
+}
+
+int lbm_launch_count(const lbm_handle *h, int64_t *launches)
+{
+    if (!h || !launches) return LBM_EINVAL;
+    *launches = h->launches;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

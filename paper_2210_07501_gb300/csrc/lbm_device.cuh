@@ -1,0 +1,332 @@
+// lbm_device.cuh -- device-side building blocks of the GB300 coupled central-moment LB
+// step (arXiv 2210.07501, Sec. 4.1-4.3, App. B): lattice constants, storage conversion,
+// pull streaming with the wall rules of Sec. 5.1, isotropic stencils and the three
+// central-moment collisions in closed form.
+//
+// Variables carried (exact affine changes of the paper's variables):
+//   f          phase-field populations, as in Sec. 4.1;
+//   g - w p0   flow populations minus the rest weights times p0 = rho_A c^2 (Sec. 4.2);
+//   h - w Tr   energy populations minus the rest weights times T_ref (Sec. 4.3);
+//   dp = p - p0.
+// The velocity is ~1e-5 of p, so the deviations keep round-off far below the signal in
+// FP64 and FP32 alike.  Equilibria are the printed ones minus the central moments of
+// the subtracted rest state, written without cancellation.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace lbm {
+
+// ---- D2Q9 velocities (Sec. 4.1; velocity 8 is (+1,-1) as in App. B's P) ----
+__host__ __device__ constexpr int ex_(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0); }
+__host__ __device__ constexpr int ey_(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
+// reversed velocity (bounce-back) and velocity mirrored in y (specular reflection)
+__host__ __device__ constexpr int opp_(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4 + 1) : ((a - 3) % 4 + 5)); }
+__host__ __device__ constexpr int mir_(int a)
+{
+    return a == 2 ? 4 : a == 4 ? 2 : a == 5 ? 8 : a == 8 ? 5 : a == 6 ? 7 : a == 7 ? 6 : a;
+}
+// weights: D2Q9 (4/9, 1/9, 1/36); D2Q5 (1/3, 1/6); c^2 = 1/3 for both
+template <int Q>
+__host__ __device__ constexpr double w_(int a)
+{
+    return Q == 9 ? (a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0)) : (a == 0 ? 1.0 / 3.0 : 1.0 / 6.0);
+}
+
+template <typename Real> struct Phys {
+    Real W4;          // 4 / W          (sharpening theta = W4 phi (1 - phi))
+    Real csf;         // 1.5 W          (delta_s = 1.5 W |grad phi|^2)
+    Real sigma0, sigma1, sigma2;
+    Real T_ref;
+    Real dTcold;      // T_cold - T_ref
+    Real rhoA, drho;  // rho(phi) = rhoA + phi drho
+    Real muA, dmu;    // mu(phi)
+    Real kA, dk;      // k(phi), c_p = 1
+    Real omega_phi, Mphi;
+    Real Fx, Fy;
+    Real g2min;       // |grad phi|^2 below which n = 0
+};
+
+template <typename Real, typename Store> struct StepArgs {
+    int nx, ny, pitch;
+    long long plane;                // ny * pitch elements per population plane
+    const Store *f_in;
+    Store *f_out;
+    const Store *g_in;
+    Store *g_out;
+    const Store *h_in;
+    Store *h_out;
+    const Real *dp_in;              // p - p0 of the previous step [ny][pitch]
+    Real *dp_out;
+    const Real *twall;              // [3][nx]: T_w - T_ref at x - 1/2, x, x + 1/2 (bottom wall)
+    double *macro;                  // optional [5][ny][nx]: phi, u, v, T, dp
+    Phys<Real> P;
+    Real sf, sg, sh;                // storage scales (value * s is stored); 1 unless FP16
+    Real isf, isg, ish;
+};
+
+// ---- storage conversion ----
+template <typename Real, typename Store>
+__device__ __forceinline__ Real ld_(const Store *p)
+{
+    if constexpr (std::is_same<Store, __half>::value)
+        return Real(__half2float(__ldg(p)));
+    else
+        return Real(__ldg(p));
+}
+template <typename Real, typename Store>
+__device__ __forceinline__ void st_(Store *p, Real v)
+{
+    if constexpr (std::is_same<Store, __half>::value)
+        *p = __float2half_rn(float(v));
+    else
+        *p = Store(v);
+}
+template <typename Store> constexpr bool scaled_() { return std::is_same<Store, __half>::value; }
+
+__device__ __forceinline__ int wrap_(int x, int n)
+{
+    int r = x % n;
+    return r < 0 ? r + n : r;
+}
+// ghost rows mirror the nearest interior rows (zero normal gradient); rows further out
+// than the stencils reach are clamped (they are never used by a lattice node)
+__device__ __forceinline__ int mirror_row_(int y, int ny)
+{
+    if (y < 0) y = -1 - y;
+    if (y >= ny) y = 2 * ny - 1 - y;
+    return y < 0 ? 0 : (y >= ny ? ny - 1 : y);
+}
+
+// ---- pull streaming with the wall rules ----
+// KIND 0: phase field, specular reflection (free slip, no flux through the wall)
+// KIND 1: flow, halfway bounce-back (no slip)
+// KIND 2: energy, anti-bounce-back to the wall temperature at the link's crossing point
+template <int KIND, int Q, typename Real, typename Store>
+__device__ __forceinline__ void pull_(const Store *__restrict__ base, long long plane, int pitch, int nx, int ny,
+                                      int x, int xm, int xp, int y, Real iscale, const Real *__restrict__ twall,
+                                      Real dTcold, Real *out)
+{
+    const long long row = (long long)y * pitch;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int ex = ex_(a), ey = ey_(a);
+        const int xs = ex > 0 ? xm : (ex < 0 ? xp : x);
+        const bool wall = (ey > 0 && y == 0) || (ey < 0 && y == ny - 1);
+        Real v;
+        if (!wall) {
+            const long long rs = ey > 0 ? row - pitch : (ey < 0 ? row + pitch : row);
+            v = ld_<Real, Store>(base + a * plane + rs + xs);
+        } else if (KIND == 0) {
+            v = ld_<Real, Store>(base + mir_(a) * plane + row + xs);
+        } else {
+            v = ld_<Real, Store>(base + opp_(a) * plane + row + x);
+        }
+        if constexpr (scaled_<Store>()) v *= iscale;
+        if (KIND == 2 && wall) {
+            // link from (x, y) towards the wall crosses it at x - e_x / 2
+            const Real tw = ey > 0 ? twall[(1 - ex) * nx + x] : dTcold;
+            v = -v + Real(2.0 * w_<Q>(a)) * tw;
+        }
+        out[a] = v;
+    }
+}
+
+// ---- isotropic finite differences on a shared-memory tile:
+// d_i psi = (1/c^2) sum_a w_a e_ai psi(x + e_a) with the D2Q9 weights ----
+template <typename Real, int LD>
+__device__ __forceinline__ void iso_grad_(const Real (*s)[LD], int y, int x, Real &gx, Real &gy)
+{
+    const Real c1 = Real(1.0 / 3.0), c2 = Real(1.0 / 12.0);
+    const Real ne = s[y + 1][x + 1], nw = s[y + 1][x - 1], se = s[y - 1][x + 1], sw = s[y - 1][x - 1];
+    gx = c1 * (s[y][x + 1] - s[y][x - 1]) + c2 * ((ne - nw) + (se - sw));
+    gy = c1 * (s[y + 1][x] - s[y - 1][x]) + c2 * ((ne - se) + (nw - sw));
+}
+template <typename Real, int LD>
+__device__ __forceinline__ Real iso_div_(const Real (*sx)[LD], const Real (*sy)[LD], int y, int x)
+{
+    const Real c1 = Real(1.0 / 3.0), c2 = Real(1.0 / 12.0);
+    const Real dx = c1 * (sx[y][x + 1] - sx[y][x - 1]) +
+                    c2 * ((sx[y + 1][x + 1] - sx[y + 1][x - 1]) + (sx[y - 1][x + 1] - sx[y - 1][x - 1]));
+    const Real dy = c1 * (sy[y + 1][x] - sy[y - 1][x]) +
+                    c2 * ((sy[y + 1][x + 1] - sy[y - 1][x + 1]) + (sy[y + 1][x - 1] - sy[y - 1][x - 1]));
+    return dx + dy;
+}
+
+template <typename Real>
+__device__ __forceinline__ void unit_normal_(Real gx, Real gy, Real g2min, Real &nx, Real &ny)
+{
+    const Real g2 = gx * gx + gy * gy;
+    if (g2 > g2min) {
+        if constexpr (std::is_same<Real, double>::value) {
+            const double m = sqrt(g2);
+            nx = gx / m;
+            ny = gy / m;
+        } else {
+            const float r = rsqrtf(g2);
+            nx = gx * r;
+            ny = gy * r;
+        }
+    } else {
+        nx = Real(0);
+        ny = Real(0);
+    }
+}
+
+// ---- App. B: central moments -> populations, F(-u) then P^-1 (D2Q9).
+// Moment order 00, 10, 01, 20, 02, 11, 21, 12, 22. ----
+template <typename Real>
+__device__ __forceinline__ void central_to_pop9_(const Real k[9], Real ux, Real uy, Real g[9])
+{
+    const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const Real r00 = k[0];
+    const Real r10 = k[1] + ux * k[0];
+    const Real r01 = k[2] + uy * k[0];
+    const Real r20 = k[3] + Real(2) * ux * k[1] + ux2 * k[0];
+    const Real r02 = k[4] + Real(2) * uy * k[2] + uy2 * k[0];
+    const Real r11 = k[5] + uy * k[1] + ux * k[2] + uxy * k[0];
+    const Real r21 = k[6] + Real(2) * ux * k[5] + uy * k[3] + ux2 * k[2] + Real(2) * uxy * k[1] + ux2 * uy * k[0];
+    const Real r12 = k[7] + Real(2) * uy * k[5] + ux * k[4] + uy2 * k[1] + Real(2) * uxy * k[2] + ux * uy2 * k[0];
+    const Real r22 = k[8] + Real(2) * ux * k[7] + Real(2) * uy * k[6] + ux2 * k[4] + uy2 * k[3] +
+                     Real(4) * uxy * k[5] + Real(2) * uxy * uy * k[1] + Real(2) * uxy * ux * k[2] + ux2 * uy2 * k[0];
+    const Real h = Real(0.5), q = Real(0.25);
+    g[0] = r00 - r20 - r02 + r22;
+    g[1] = h * (r10 + r20 - r12 - r22);
+    g[2] = h * (r01 + r02 - r21 - r22);
+    g[3] = h * (-r10 + r20 + r12 - r22);
+    g[4] = h * (-r01 + r02 + r21 - r22);
+    g[5] = q * (r11 + r21 + r12 + r22);
+    g[6] = q * (-r11 + r21 - r12 + r22);
+    g[7] = q * (r11 - r21 - r12 + r22);
+    g[8] = q * (-r11 - r21 + r12 + r22);
+}
+
+// D2Q5 analogue: basis 1, e_x, e_y, e_x^2, e_y^2 (the first five rows of F(-u)).
+template <typename Real>
+__device__ __forceinline__ void central_to_pop5_(const Real k[5], Real ux, Real uy, Real f[5])
+{
+    const Real r00 = k[0];
+    const Real r10 = k[1] + ux * k[0];
+    const Real r01 = k[2] + uy * k[0];
+    const Real r20 = k[3] + Real(2) * ux * k[1] + ux * ux * k[0];
+    const Real r02 = k[4] + Real(2) * uy * k[2] + uy * uy * k[0];
+    const Real h = Real(0.5);
+    f[0] = r00 - r20 - r02;
+    f[1] = h * (r10 + r20);
+    f[2] = h * (r01 + r02);
+    f[3] = h * (r20 - r10);
+    f[4] = h * (r02 - r01);
+}
+
+template <int Q, typename Real>
+__device__ __forceinline__ void raw_first_(const Real *p, Real &m10, Real &m01)
+{
+    if constexpr (Q == 9) {
+        m10 = (p[1] - p[3]) + ((p[5] - p[6]) + (p[8] - p[7]));
+        m01 = (p[2] - p[4]) + ((p[5] + p[6]) - (p[7] + p[8]));
+    } else {
+        m10 = p[1] - p[3];
+        m01 = p[2] - p[4];
+    }
+}
+
+// ---- Sec. 4.1 phase-field collision: first central moments relax at omega_phi towards
+// M_phi theta n, the rest take their equilibria (phi, c^2 phi, c^2 phi, 0, 0, 0, c^4 phi).
+template <int Q, typename Real>
+__device__ __forceinline__ void collide_phase_(Real *f, Real phi, Real ux, Real uy, Real mx, Real my, Real om)
+{
+    Real m10, m01;
+    raw_first_<Q>(f, m10, m01);
+    const Real k10 = m10 - ux * phi, k01 = m01 - uy * phi;
+    const Real t10 = k10 + om * (mx - k10), t01 = k01 + om * (my - k01);
+    const Real c2p = phi * Real(1.0 / 3.0);
+    if constexpr (Q == 9) {
+        const Real k[9] = {phi, t10, t01, c2p, c2p, Real(0), Real(0), Real(0), phi * Real(1.0 / 9.0)};
+        central_to_pop9_(k, ux, uy, f);
+    } else {
+        const Real k[5] = {phi, t10, t01, c2p, c2p};
+        central_to_pop5_(k, ux, uy, f);
+    }
+}
+
+// ---- Sec. 4.3 energy collision on h - w T_ref: first central moments relax at omega_T;
+// the rest take (T E - T_ref Wc(u)) = dT E + T_ref D(u), where E = (1,0,0,c^2,c^2,0,0,0,c^4)
+// are the Maxwellian central moments per unit T and Wc(u) those of the weights. ----
+template <int Q, typename Real>
+__device__ __forceinline__ void collide_energy_(Real *h, Real dT, Real ux, Real uy, Real Tr, Real om)
+{
+    Real m10, m01;
+    raw_first_<Q>(h, m10, m01);
+    const Real k10 = m10 - ux * dT, k01 = m01 - uy * dT;
+    const Real t10 = k10 + om * (Tr * ux - k10), t01 = k01 + om * (Tr * uy - k01);
+    const Real c2 = Real(1.0 / 3.0);
+    const Real ux2 = ux * ux, uy2 = uy * uy;
+    if constexpr (Q == 9) {
+        const Real k[9] = {dT,
+                           t10,
+                           t01,
+                           c2 * dT - Tr * ux2,
+                           c2 * dT - Tr * uy2,
+                           -Tr * ux * uy,
+                           Tr * (c2 + ux2) * uy,
+                           Tr * (c2 + uy2) * ux,
+                           Real(1.0 / 9.0) * dT - Tr * (c2 * (ux2 + uy2) + ux2 * uy2)};
+        central_to_pop9_(k, ux, uy, h);
+    } else {
+        const Real k[5] = {dT, t10, t01, c2 * dT - Tr * ux2, c2 * dT - Tr * uy2};
+        central_to_pop5_(k, ux, uy, h);
+    }
+}
+
+// ---- Sec. 4.2 two-fluid collision on g - w p0.  Only the trace-free second moment 2d
+// and 11 relax at omega_nu (pre-collision values needed); every other central moment
+// is replaced by equilibrium + source / 2.  Deviation equilibrium:
+//   eta^eq - p0 Wc(u) = dp Wc(u) + rho c^2 D(u). ----
+template <typename Real>
+__device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real ux, Real uy, Real Fpx, Real Fpy,
+                                              Real Ftx, Real Fty, Real om, Real s0, Real sx, Real sy)
+{
+    const Real c2 = Real(1.0 / 3.0), hf = Real(0.5);
+    const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    // pre-collision central moments 20, 02, 11 (F(u) rows on the raw moments)
+    const Real r20 = (g[1] + g[3]) + ((g[5] + g[6]) + (g[7] + g[8]));
+    const Real r02 = (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8]));
+    const Real r11 = (g[5] - g[6]) + (g[7] - g[8]);
+    const Real e20 = r20 - Real(2) * ux * sx + ux2 * s0;
+    const Real e02 = r02 - Real(2) * uy * sy + uy2 * s0;
+    const Real e11 = r11 - uy * sx - ux * sy + uxy * s0;
+    // deviation equilibrium
+    const Real ax = c2 + ux2, ay = c2 + uy2, rc2 = rho * c2, d = rc2 - dp;
+    const Real q00 = dp, q10 = ux * d, q01 = uy * d;
+    const Real q20 = dp * ax - rc2 * ux2, q02 = dp * ay - rc2 * uy2;
+    const Real q11 = -uxy * d;
+    const Real q21 = ax * uy * d, q12 = ay * ux * d;
+    const Real q22 = dp * ax * ay - rc2 * (c2 * (ux2 + uy2) + ux2 * uy2);
+    // source central moments, Gamma = F_p . u
+    const Real G = Fpx * ux + Fpy * uy;
+    const Real s00 = G, s10 = c2 * Ftx - ux * G, s01 = c2 * Fty - uy * G;
+    const Real s20 = Real(2) * c2 * Fpx * ux + ax * G, s02 = Real(2) * c2 * Fpy * uy + ay * G;
+    const Real s11 = c2 * (Fpx * uy + Fpy * ux) + uxy * G;
+    // relaxation (2s at 1, 2d and 11 at omega_nu, all others at 1)
+    const Real sw = Real(1) - hf * om;
+    const Real t2s = (q20 + q02) + hf * (s20 + s02);
+    const Real e2d = e20 - e02;
+    const Real t2d = e2d + om * ((q20 - q02) - e2d) + sw * (s20 - s02);
+    Real k[9];
+    k[0] = q00 + hf * s00;
+    k[1] = q10 + hf * s10;
+    k[2] = q01 + hf * s01;
+    k[3] = hf * (t2s + t2d);
+    k[4] = hf * (t2s - t2d);
+    k[5] = e11 + om * (q11 - e11) + sw * s11;
+    k[6] = q21;
+    k[7] = q12;
+    k[8] = q22;
+    central_to_pop9_(k, ux, uy, g);
+}
+
+}  // namespace lbm

@@ -1,0 +1,36 @@
+// lbm_internal.h -- launchers shared between the kernel and the host translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <typename Real, typename Store, int QF, int QT>
+cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s);
+
+// Initialisation: macro [5][ny][nx] (phi, u, v, T, dp) holds the fields; entries whose
+// bit in `defaults` (1 phi, 2 u, 4 v, 8 T, 16 dp) is set are filled with the defaults
+// first.  Then the populations are set to the central-moment equilibria.
+template <typename Real, typename Store, int QF, int QT>
+cudaError_t launch_init(const StepArgs<Real, Store> &A, double b, double W, int defaults, cudaStream_t s);
+
+// Reductions over the macro fields: partials[nblk][4] then result[4] =
+// (sum phi, sum |u - u_prev|^2, sum |u|^2, non-finite count); u_prev <- u if update.
+cudaError_t launch_reduce(const double *macro, double *uprev, long long N, int update, double *partials,
+                          int nblk, double *result, cudaStream_t s);
+int reduce_blocks();
+
+// [Q][ny][nx] doubles <-> [Q][ny][pitch] storage (value * scale stored)
+template <typename Real, typename Store>
+cudaError_t launch_to_store(const double *src, Store *dst, int Q, int nx, int ny, int pitch, Real scale,
+                            cudaStream_t s);
+template <typename Real, typename Store>
+cudaError_t launch_from_store(const Store *src, double *dst, int Q, int nx, int ny, int pitch, Real iscale,
+                              cudaStream_t s);
+// macro plane -> device array of float or double
+cudaError_t launch_export(const double *src, void *dst, long long N, int to_float, cudaStream_t s);
+
+}  // namespace lbm

