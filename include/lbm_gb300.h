@@ -141,6 +141,36 @@ int lbm_bytes_per_node(const lbm_handle *h, int64_t *bytes);
 /* Number of step-kernel launches queued since creation (diagnostics). */
 int lbm_launch_count(const lbm_handle *h, int64_t *launches);
 
+/* Largest node count lbm_reduce_fields_noalloc accepts. */
+#define LBM_NOALLOC_MAX_NODES 2147483647LL
+
+/* Field reductions for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a service of the library.  Who needs it: code that queues work
+ * while its stream is being captured into a CUDA graph (cudaMalloc is not allowed there),
+ * and plugins or custom calls inside a framework that owns every device allocation and
+ * only hands over buffers.  The function allocates nothing: the caller passes the inputs
+ * and the output, and the partial sums go to a 9.5 KiB scratch array compiled into the
+ * library, which every GPU that loads the library keeps until the process exits.
+ *
+ * Inputs are caller-owned device arrays of n_nodes doubles (e.g. the fields written by
+ * lbm_fields_device): phi, u, v, T, and optionally the velocity of an earlier step u_prev,
+ * v_prev (both NULL: taken as zero).  result is a caller-owned device array of 4 doubles,
+ * written on `stream` (a cudaStream_t; NULL = the legacy default stream):
+ *   result[0] = sum phi, result[1] = sum (u - u_prev)^2 + (v - v_prev)^2,
+ *   result[2] = sum u^2 + v^2, result[3] = number of nodes with a non-finite value,
+ * summed in FP64 in the same fixed order as lbm_diag, so both give the same values.
+ * Returns LBM_EINVAL for NULL inputs, for only one of u_prev / v_prev, or for n_nodes
+ * outside 1 .. LBM_NOALLOC_MAX_NODES; LBM_ECUDA if a launch fails.  Asynchronous.
+ *
+ * The first call on each device looks up the scratch array's device address (with that
+ * device current) and caches it; make that first call before any stream capture begins.
+ * All calls on a device share the one scratch array: calls that overlap on the GPU (for
+ * example on two streams at once) race and give wrong sums; serialise them.  Every call
+ * overwrites all the scratch it reads, so leftovers of an earlier call do no harm. */
+int lbm_reduce_fields_noalloc(const double *phi, const double *u, const double *v, const double *T,
+                              const double *u_prev, const double *v_prev, int64_t n_nodes, double *result,
+                              void *stream);
+
 /* Release the handle and its device memory; NULL-safe. */
 void lbm_destroy(lbm_handle *h);
 

@@ -68,6 +68,8 @@ SIGNATURES = {
     "lbm_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
     "lbm_bytes_per_node": (ctypes.c_int, [_H, _I64P]),
     "lbm_launch_count": (ctypes.c_int, [_H, _I64P]),
+    "lbm_reduce_fields_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_void_p,
+                                                                      ctypes.c_void_p]),
     "lbm_destroy": (None, [_H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
