@@ -262,6 +262,11 @@ def bench_gpu(args):
         g = pkg.Lbm(w["domain"], w["params"], precision=PRECISION, stream=stream)
         g.lbm_set_check_interval(CHECK_INTERVAL)
         bpn = g.lbm_bytes_per_node()
+        if args.segment:
+            g.lbm_set_segment(args.segment)
+            seg_rows = args.segment
+        else:
+            seg_rows = g.lbm_autotune(10)    # launch shape; leaves the state untouched
         # ---- device-resident throughput ----
         g.lbm_step(args.warmup)
         torch.cuda.synchronize()
@@ -296,11 +301,12 @@ def bench_gpu(args):
         "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "b": w["domain"]["b"], "W": w["domain"]["W"],
                    "lattices": "D2Q9 flow + D2Q5 phase field + D2Q5 energy", "storage": PRECISION,
                    "check_interval": CHECK_INTERVAL, "l2": "working set 2.7 GB > L2 (no flush needed)",
+                   "segment_rows": seg_rows,
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(),
                      "bytes_per_node": bpn, "peak_source": peak_kind,
-                     "kernel": "lbm::step_kernel<float,float,5,5> (+ reductions every 100 steps in the region)"},
+                     "kernel": "lbm::march_kernel<float,float,5,5,256> (+ reductions every 100 steps in the region)"},
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
@@ -327,6 +333,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--ny", type=int, default=0, help="rows of a shorter channel (profiling); 0 = full")
+    ap.add_argument("--segment", type=int, default=0, help="rows per CTA segment; 0 = autotune")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

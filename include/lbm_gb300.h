@@ -61,7 +61,7 @@ typedef struct lbm_handle lbm_handle;
 
 /* Lattice and discretisation (Sec. 2.1, Sec. 4). */
 typedef struct {
-    int32_t nx, ny;        /* nodes; nx >= 3, ny >= 3, nx * ny <= 2^31                    */
+    int32_t nx, ny;        /* nodes; nx >= 3, ny >= 3, ny * (nx rounded up to 64) < 2^31 */
     int32_t heat_periods;  /* cosine periods of the bottom-wall temperature along x (>= 0) */
     int32_t q_phi;         /* 5 or 9: phase-field lattice                                  */
     int32_t q_T;           /* 5 or 9: energy lattice                                       */
@@ -133,6 +133,17 @@ int lbm_set_state(lbm_handle *h, const double *f, const double *g, const double 
  * restores the state bit for bit.  LBM_EIO on a missing, truncated or corrupt file. */
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
+
+/* Launch shape of the step kernel: each CTA walks `rows` consecutive rows of a strip
+ * (0 = automatic: chosen from the device's occupancy so the grid is a whole number of
+ * waves).  Affects speed only, never the results. */
+int lbm_set_segment(lbm_handle *h, int32_t rows);
+
+/* Autotuner: times `reps` launches of the step kernel for each candidate segment length
+ * (automatic, 8 .. 256 rows below ny) and keeps the fastest; *rows (may be NULL) receives
+ * it.  The kernel is re-launched from the same input buffer, so the state and the step
+ * count are unchanged.  Synchronises. */
+int lbm_autotune(lbm_handle *h, int32_t reps, int32_t *rows);
 
 /* Bytes the step kernel moves per lattice node and step (populations read and written
  * once plus the stored pressure), for roofline accounting. */

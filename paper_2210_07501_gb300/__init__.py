@@ -66,6 +66,8 @@ SIGNATURES = {
     "lbm_set_state": (ctypes.c_int, [_H, _D, _D, _D, _D]),
     "lbm_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
+    "lbm_set_segment": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "lbm_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "lbm_bytes_per_node": (ctypes.c_int, [_H, _I64P]),
     "lbm_launch_count": (ctypes.c_int, [_H, _I64P]),
     "lbm_reduce_fields_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_void_p,
@@ -220,6 +222,14 @@ class Lbm:
 
     def lbm_load(self, path: str):
         _check(self._lib.lbm_load(self._h, os.fsencode(path)), "lbm_load")
+
+    def lbm_set_segment(self, rows: int):
+        _check(self._lib.lbm_set_segment(self._h, int(rows)), "lbm_set_segment")
+
+    def lbm_autotune(self, reps: int = 20) -> int:
+        r = ctypes.c_int32()
+        _check(self._lib.lbm_autotune(self._h, int(reps), ctypes.byref(r)), "lbm_autotune")
+        return r.value
 
     def lbm_bytes_per_node(self) -> int:
         b = ctypes.c_int64()

@@ -37,6 +37,7 @@ struct lbm_handle {
     double *staging;        // lazily allocated [9][ny][nx] doubles for state I/O
     int cur;
     int64_t step, check_interval, launches;
+    int seg_rows;           // rows per CTA segment of the step kernel (0 = automatic)
     int64_t last_check_step, prev_check_step;
     bool have_check, have_prev_check;
     double res_du2, res_u2;
@@ -99,6 +100,15 @@ template <typename Real, typename Store> static StepArgs<Real, Store> make_args(
     A.dp_out = (Real *)h->dp[dst];
     A.twall = (const Real *)h->twall;
     A.macro = macro;
+    for (int a = 0; a < 9; ++a) {
+        const long long o = (long long)a * h->plane;
+        A.fi[a] = A.f_in + (a < h->Qf ? o : 0);
+        A.gi[a] = A.g_in + o;
+        A.hi[a] = A.h_in + (a < h->Qt ? o : 0);
+        A.fo[a] = A.f_out + (a < h->Qf ? o : 0);
+        A.go[a] = A.g_out + o;
+        A.ho[a] = A.h_out + (a < h->Qt ? o : 0);
+    }
     A.P = cast_phys<Real>(h->P);
     A.sf = Real(h->sf);
     A.sg = Real(h->sg);
@@ -130,7 +140,7 @@ static cudaError_t dispatch(const lbm_handle *h, Args... args)
 template <typename R, typename S, int QF, int QT> struct StepFn {
     static cudaError_t run(const lbm_handle *h, int src, double *macro)
     {
-        return launch_step<R, S, QF, QT>(make_args<R, S>(h, src, macro), h->stream);
+        return launch_step<R, S, QF, QT>(make_args<R, S>(h, src, macro), h->stream, h->seg_rows);
     }
 };
 template <typename R, typename S, int QF, int QT> struct InitFn {
@@ -165,7 +175,9 @@ static void free_all(lbm_handle *h)
 static int validate(const lbm_domain *d, const lbm_params *p)
 {
     if (!d || !p) return LBM_EINVAL;
-    if (d->nx < 3 || d->ny < 3 || (long long)d->nx * d->ny > (1LL << 31)) return LBM_EINVAL;
+    if (d->nx < 3 || d->ny < 3) return LBM_EINVAL;
+    // element offsets inside one population plane are 32-bit
+    if ((long long)d->ny * (((long long)d->nx + 63) / 64 * 64) >= (1LL << 31)) return LBM_EINVAL;
     if ((d->q_phi != 5 && d->q_phi != 9) || (d->q_T != 5 && d->q_T != 9)) return LBM_EINVAL;
     if (d->precision < LBM_FP64 || d->precision > LBM_FP16 || d->heat_periods < 0) return LBM_EINVAL;
     if (!(d->W > 0.0) || !(d->b > 0.0) || !(d->b < d->ny)) return LBM_EINVAL;
@@ -620,6 +632,50 @@ int lbm_load(lbm_handle *h, const char *path)
     if (e != cudaSuccess) return cuda_fail(e, "lbm_load copy");
     h->step = hd.step;
     return reset_diag(h);
+}
+
+int lbm_set_segment(lbm_handle *h, int32_t rows)
+{
+    if (!h || rows < 0) return LBM_EINVAL;
+    h->seg_rows = rows;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle *h, int32_t reps, int32_t *rows)
+{
+    if (!h || reps < 1) return LBM_EINVAL;
+    // candidates: automatic, then fixed segment lengths up to the channel height
+    int cand[16], nc = 0;
+    cand[nc++] = 0;
+    const int fixed[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
+    for (int f : fixed)
+        if (f < h->ny && nc < 16) cand[nc++] = f;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int saved = h->seg_rows;
+    float best_ms = 1e30f;
+    int best = 0;
+    int rc = LBM_OK;
+    for (int k = 0; k < nc && rc == LBM_OK; ++k) {
+        h->seg_rows = cand[k];
+        // the kernel reads buffer cur and writes the other one; launching it again from
+        // the same buffer leaves the state and the step count untouched
+        cudaError_t e = dispatch<StepFn>(h, h->cur, (double *)nullptr);      // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch<StepFn>(h, h->cur, (double *)nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "lbm_autotune"); break; }
+        if (ms < best_ms) { best_ms = ms; best = cand[k]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->seg_rows = rc == LBM_OK ? best : saved;
+    if (rows) *rows = h->seg_rows;
+    return rc;
 }
 
 int lbm_bytes_per_node(const lbm_handle *h, int64_t *bytes)

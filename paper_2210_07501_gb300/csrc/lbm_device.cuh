@@ -64,6 +64,9 @@ template <typename Real, typename Store> struct StepArgs {
     Real *dp_out;
     const Real *twall;              // [3][nx]: T_w - T_ref at x - 1/2, x, x + 1/2 (bottom wall)
     double *macro;                  // optional [5][ny][nx]: phi, u, v, T, dp
+    // per-population plane base pointers (plane a of lattice X starts at X_in + a * plane)
+    const Store *fi[9], *gi[9], *hi[9];
+    Store *fo[9], *go[9], *ho[9];
     Phys<Real> P;
     Real sf, sg, sh;                // storage scales (value * s is stored); 1 unless FP16
     Real isf, isg, ish;

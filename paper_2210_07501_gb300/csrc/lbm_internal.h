@@ -8,8 +8,10 @@
 
 namespace lbm {
 
+// One time step from A's input buffers to its output buffers.  seg_rows > 0 sets the
+// number of rows each CTA marches through; 0 picks it from the occupancy (whole waves).
 template <typename Real, typename Store, int QF, int QT>
-cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s);
+cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_rows);
 
 // Initialisation: macro [5][ny][nx] (phi, u, v, T, dp) holds the fields; entries whose
 // bit in `defaults` (1 phi, 2 u, 4 v, 8 T, 16 dp) is set are filled with the defaults

@@ -271,3 +271,25 @@ def test_full_size_8192x2048(pkg, orc, precision):
     a, b, bars = run_pair(pkg, orc, w, 3, precision=precision, init=init, with_bars=True)
     for k in FIELDS:
         assert rel_l2(a[k], b[k]) <= bars[k], (k, rel_l2(a[k], b[k]), bars[k])
+
+
+def test_segment_length_and_autotune_do_not_change_results(pkg):
+    """The launch shape (rows per CTA) changes speed only: results are bit-identical, and
+    the autotuner leaves the state and the step count untouched."""
+    w = WL.channel(300, 70, 30.0, W=4.0, sigma1=1e-4, sigma2=-3e-4)
+    out = []
+    for seg in (0, 8, 13, 64, -1):
+        g = pkg.Lbm(w["domain"], w["params"], precision="fp32")
+        g.lbm_step(7)
+        if seg >= 0:
+            g.lbm_set_segment(seg)
+        else:
+            chosen = g.lbm_autotune(3)
+            assert chosen >= 0
+            assert g.lbm_diag()["step"] == 7
+        g.lbm_step(50)
+        out.append(g.lbm_fields())
+        g.close()
+    for o in out[1:]:
+        for k in FIELDS:
+            assert np.array_equal(o[k], out[0][k]), k
