@@ -182,6 +182,43 @@ int lbm_reduce_fields_noalloc(const double *phi, const double *u, const double *
                               const double *u_prev, const double *v_prev, int64_t n_nodes, double *result,
                               void *stream);
 
+/* ---- batched parameter sweeps (many channels of uneven size, one launch per step) ---- */
+typedef struct lbm_batch lbm_batch;
+
+/* Create n independent channels (domains[c], params[c]; all with the same precision, q_phi
+ * and q_T), each initialised as lbm_create does.  One step of the batch is one launch of
+ * the step kernel over the strips of every still-active channel; chunks of K steps (one
+ * residual check each) are captured once into a CUDA graph and replayed.  `stream` as in
+ * lbm_create.  This is the batched sweep over (sigma1, sigma2, a/b, k~, mu~) of Sec. 6. */
+int lbm_batch_create(int32_t n, const lbm_domain *domains, const lbm_params *params, void *stream, lbm_batch **out);
+
+/* Steps per chunk and residual check (even, >= 2; default 100). */
+int lbm_batch_set_check_interval(lbm_batch *b, int32_t K);
+
+/* Autotuner for the batch launch: times `reps` launches per candidate segment length and
+ * keeps the fastest (state untouched); *rows receives it.  Synchronises. */
+int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *rows);
+
+/* Advance every active channel by nsteps (a multiple of K).  Synchronises after every
+ * chunk to read the per-channel residuals; LBM_EUNSTABLE if a channel went non-finite. */
+int lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Step until every channel has residual <= tol (a converged channel stops being stepped)
+ * or max_steps have been taken; steps[c] and converged[c] (arrays of n; may be NULL)
+ * receive each channel's step count and status.  LBM_OK if all converged, else
+ * LBM_ETIMEOUT (or an error). */
+int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int64_t *steps, int32_t *converged);
+
+/* Fields, residual and step count of channel c (as lbm_fields); lbm_batch_init_fields
+ * re-initialises channel c from host fields (as lbm_init_fields) and re-activates it. */
+int lbm_batch_fields(lbm_batch *b, int32_t c, double *phi, double *u, double *v, double *T, double *dp);
+int lbm_batch_diag(lbm_batch *b, int32_t c, double *residual, int64_t *steps);
+int lbm_batch_init_fields(lbm_batch *b, int32_t c, const double *phi, const double *u, const double *v,
+                          const double *T, const double *dp);
+/* Number of channels, CTAs per batch launch and rows per CTA segment. */
+int lbm_batch_size(const lbm_batch *b, int32_t *n, int32_t *ctas, int32_t *rows);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Release the handle and its device memory; NULL-safe. */
 void lbm_destroy(lbm_handle *h);
 

@@ -72,6 +72,19 @@ SIGNATURES = {
     "lbm_launch_count": (ctypes.c_int, [_H, _I64P]),
     "lbm_reduce_fields_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_void_p,
                                                                       ctypes.c_void_p]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(LbmDomain), ctypes.POINTER(LbmParams),
+                                        ctypes.c_void_p, ctypes.POINTER(_H)]),
+    "lbm_batch_set_check_interval": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "lbm_batch_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_step": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "lbm_batch_run_to_steady": (ctypes.c_int, [_H, ctypes.c_double, ctypes.c_int64, _I64P,
+                                               ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_fields": (ctypes.c_int, [_H, ctypes.c_int32, _D, _D, _D, _D, _D]),
+    "lbm_batch_diag": (ctypes.c_int, [_H, ctypes.c_int32, _D, _I64P]),
+    "lbm_batch_init_fields": (ctypes.c_int, [_H, ctypes.c_int32, _D, _D, _D, _D, _D]),
+    "lbm_batch_size": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_destroy": (None, [_H]),
     "lbm_destroy": (None, [_H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -248,3 +261,75 @@ class Lbm:
     init_fields = lbm_init_fields
     get_state = lbm_get_state
     set_state = lbm_set_state
+
+
+class LbmBatch:
+    """Many channels of uneven size stepped together (one lbm_batch)."""
+
+    def __init__(self, workloads: list, precision="fp32", stream=None):
+        self._lib = load()
+        self.workloads = [dict(w) for w in workloads]
+        n = len(workloads)
+        doms = (LbmDomain * n)(*[make_domain(w["domain"], precision) for w in workloads])
+        prms = (LbmParams * n)(*[make_params(w["params"]) for w in workloads])
+        self.n = n
+        self.shapes = [(int(w["domain"]["ny"]), int(w["domain"]["nx"])) for w in workloads]
+        self._h = _H()
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        _check(self._lib.lbm_batch_create(n, doms, prms, s, ctypes.byref(self._h)), "lbm_batch_create")
+
+    def lbm_batch_destroy(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = _H()
+
+    close = lbm_batch_destroy
+
+    def __del__(self):
+        try:
+            self.lbm_batch_destroy()
+        except Exception:
+            pass
+
+    def lbm_batch_set_check_interval(self, K: int):
+        _check(self._lib.lbm_batch_set_check_interval(self._h, int(K)), "lbm_batch_set_check_interval")
+
+    def lbm_batch_autotune(self, reps: int = 10) -> int:
+        r = ctypes.c_int32()
+        _check(self._lib.lbm_batch_autotune(self._h, int(reps), ctypes.byref(r)), "lbm_batch_autotune")
+        return r.value
+
+    def lbm_batch_step(self, n: int):
+        _check(self._lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def lbm_batch_run_to_steady(self, tol: float, max_steps: int):
+        steps = (ctypes.c_int64 * self.n)()
+        conv = (ctypes.c_int32 * self.n)()
+        rc = self._lib.lbm_batch_run_to_steady(self._h, float(tol), int(max_steps), steps, conv)
+        if rc not in (LBM_OK, LBM_ETIMEOUT):
+            _check(rc, "lbm_batch_run_to_steady")
+        return list(steps), [bool(c) for c in conv]
+
+    def lbm_batch_fields(self, c: int) -> dict:
+        shape = self.shapes[c]
+        out = {k: np.empty(shape) for k in ("phi", "u", "v", "T", "dp")}
+        _check(self._lib.lbm_batch_fields(self._h, int(c), *[_dptr(out[k]) for k in ("phi", "u", "v", "T", "dp")]),
+               "lbm_batch_fields")
+        return out
+
+    def lbm_batch_diag(self, c: int):
+        r, st = ctypes.c_double(), ctypes.c_int64()
+        _check(self._lib.lbm_batch_diag(self._h, int(c), ctypes.byref(r), ctypes.byref(st)), "lbm_batch_diag")
+        return {"residual": r.value, "steps": st.value}
+
+    def lbm_batch_init_fields(self, c: int, phi=None, u=None, v=None, T=None, dp=None):
+        shape = self.shapes[c]
+        a = [_field(x, shape) for x in (phi, u, v, T, dp)]
+        _check(self._lib.lbm_batch_init_fields(self._h, int(c), *[_dptr(x) for x in a]), "lbm_batch_init_fields")
+
+    def lbm_batch_size(self):
+        n, c, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lbm_batch_size(self._h, ctypes.byref(n), ctypes.byref(c), ctypes.byref(r)), "lbm_batch_size")
+        return {"cases": n.value, "ctas": c.value, "rows": r.value}

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/lbm_gb300.h"
 #include "lbm_internal.h"
@@ -698,6 +699,321 @@ void lbm_destroy(lbm_handle *h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_all(h);
     delete h;
+}
+
+}  // extern "C"
+
+// ======================================================================================
+// Batched sweep: many channels of uneven size stepped by one kernel launch per step.
+// ======================================================================================
+
+struct lbm_batch {
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_handle *> h;       // per-case state (allocated on the batch stream)
+    void *d_args[2] = {nullptr, nullptr};   // StepArgs per case, source buffer 0 / 1, no macros
+    void *d_args_m[2] = {nullptr, nullptr}; // same, writing the macroscopic fields
+    int4 *d_ctas = nullptr;
+    int n_ctas = 0, seg = 32;
+    int *d_active = nullptr;
+    std::vector<int> active;
+    double *d_results = nullptr;       // [n][4] reduction results of the last check
+    double *h_results = nullptr;       // pinned copy
+    std::vector<int64_t> steps;        // steps taken per case
+    std::vector<double> residual;      // last residual per case (-1 before two checks)
+    std::vector<int> checks;
+    int64_t K = 100;                   // steps per chunk (even), one residual check per chunk
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+};
+
+template <typename R, typename S, int QF, int QT> struct BatchArgsFn {
+    static cudaError_t run(const lbm_handle *, lbm_batch *b)
+    {
+        const size_t sz = sizeof(StepArgs<R, S>);
+        std::vector<StepArgs<R, S>> a(b->n);
+        for (int par = 0; par < 2; ++par)
+            for (int m = 0; m < 2; ++m) {
+                for (int c = 0; c < b->n; ++c) a[c] = make_args<R, S>(b->h[c], par, m ? b->h[c]->macro : nullptr);
+                void *&dst = m ? b->d_args_m[par] : b->d_args[par];
+                if (!dst) {
+                    cudaError_t e = cudaMalloc(&dst, sz * b->n);
+                    if (e != cudaSuccess) return e;
+                }
+                cudaError_t e = cudaMemcpy(dst, a.data(), sz * b->n, cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return e;
+            }
+        return cudaSuccess;
+    }
+};
+
+template <typename R, typename S, int QF, int QT> struct BatchTableFn {
+    static cudaError_t run(const lbm_handle *, lbm_batch *b, int seg)
+    {
+        const int TX = step_strip_width<R, S, QF, QT>();
+        std::vector<int4> t;
+        for (int c = 0; c < b->n; ++c) {
+            const int strips = (b->h[c]->nx + TX - 1) / TX, segs = (b->h[c]->ny + seg - 1) / seg;
+            for (int by = 0; by < segs; ++by)
+                for (int bx = 0; bx < strips; ++bx) t.push_back(make_int4(c, bx, by, 0));
+        }
+        if (b->d_ctas) cudaFree(b->d_ctas);
+        b->d_ctas = nullptr;
+        cudaError_t e = cudaMalloc((void **)&b->d_ctas, t.size() * sizeof(int4));
+        if (e != cudaSuccess) return e;
+        b->n_ctas = (int)t.size();
+        b->seg = seg;
+        return cudaMemcpy(b->d_ctas, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+};
+
+template <typename R, typename S, int QF, int QT> struct BatchStepFn {
+    static cudaError_t run(const lbm_handle *, lbm_batch *b, int par, int macro)
+    {
+        const StepArgs<R, S> *args = (const StepArgs<R, S> *)(macro ? b->d_args_m[par] : b->d_args[par]);
+        return launch_batch<R, S, QF, QT>(args, b->d_ctas, b->n_ctas, b->d_active, b->seg, b->stream);
+    }
+};
+
+template <typename R, typename S, int QF, int QT> struct BatchSlotsFn {
+    static cudaError_t run(const lbm_handle *, int *slots)
+    {
+        *slots = resident_ctas<R, S, QF, QT>();
+        return cudaSuccess;
+    }
+};
+
+static int batch_capture(lbm_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_valid = false;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < b->K && e == cudaSuccess; ++k)
+        e = dispatch<BatchStepFn>(b->h[0], b, (int)(k & 1), (int)(k == b->K - 1));
+    for (int c = 0; c < b->n && e == cudaSuccess; ++c) {
+        lbm_handle *h = b->h[c];
+        e = launch_reduce(h->macro, h->uprev, (long long)h->nx * h->ny, 1, h->partials, reduce_blocks(),
+                          b->d_results + 4 * c, b->stream);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "batch capture"); }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    b->graph_valid = true;
+    return LBM_OK;
+}
+
+extern "C" {
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int p = 0; p < 2; ++p) {
+        if (b->d_args[p]) cudaFree(b->d_args[p]);
+        if (b->d_args_m[p]) cudaFree(b->d_args_m[p]);
+    }
+    if (b->d_ctas) cudaFree(b->d_ctas);
+    if (b->d_active) cudaFree(b->d_active);
+    if (b->d_results) cudaFree(b->d_results);
+    if (b->h_results) cudaFreeHost(b->h_results);
+    for (lbm_handle *h : b->h) lbm_destroy(h);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int lbm_batch_create(int32_t n, const lbm_domain *domains, const lbm_params *params, void *stream, lbm_batch **out)
+{
+    if (!out || n < 1 || !domains || !params) return LBM_EINVAL;
+    *out = nullptr;
+    for (int c = 0; c < n; ++c) {
+        int rc = validate(&domains[c], &params[c]);
+        if (rc) return rc;
+        if (domains[c].precision != domains[0].precision || domains[c].q_phi != domains[0].q_phi ||
+            domains[c].q_T != domains[0].q_T)
+            return LBM_EINVAL;
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ENOMEM;
+    b->n = n;
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+        b->own_stream = true;
+    }
+    for (int c = 0; c < n; ++c) {
+        lbm_handle *h = nullptr;
+        int rc = lbm_create(&domains[c], &params[c], (void *)b->stream, &h);
+        if (rc) { lbm_batch_destroy(b); return rc; }
+        b->h.push_back(h);
+    }
+    b->active.assign(n, 1);
+    b->steps.assign(n, 0);
+    b->residual.assign(n, -1.0);
+    b->checks.assign(n, 0);
+    bool ok = cudaMalloc((void **)&b->d_active, n * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_results, 4 * (size_t)n * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_results, 4 * (size_t)n * sizeof(double)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); lbm_batch_destroy(b); return LBM_ENOMEM; }
+    cudaError_t e = cudaMemcpy(b->d_active, b->active.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dispatch<BatchArgsFn>(b->h[0], b);
+    int slots = 0;
+    if (e == cudaSuccess) e = dispatch<BatchSlotsFn>(b->h[0], &slots);
+    if (e == cudaSuccess) e = dispatch<BatchTableFn>(b->h[0], b, 32);
+    if (e != cudaSuccess) { int rc = cuda_fail(e, "lbm_batch_create"); lbm_batch_destroy(b); return rc; }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_check_interval(lbm_batch *b, int32_t K)
+{
+    if (!b || K < 2 || (K & 1)) return LBM_EINVAL;
+    b->K = K;
+    b->graph_valid = false;
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch *b, int32_t reps, int32_t *rows)
+{
+    if (!b || reps < 1) return LBM_EINVAL;
+    int maxny = 0;
+    for (lbm_handle *h : b->h) maxny = h->ny > maxny ? h->ny : maxny;
+    const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = b->seg, rc = LBM_OK;
+    for (int seg : cand) {
+        if (seg > maxny && seg != cand[0]) continue;
+        cudaError_t e = dispatch<BatchTableFn>(b->h[0], b, seg);
+        // launches from buffer 0 into buffer 1 leave the state (in buffer 0) untouched
+        if (e == cudaSuccess) e = dispatch<BatchStepFn>(b->h[0], b, 0, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch<BatchStepFn>(b->h[0], b, 0, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "lbm_batch_autotune"); break; }
+        if (ms < best_ms) { best_ms = ms; best = seg; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == LBM_OK) {
+        cudaError_t e = dispatch<BatchTableFn>(b->h[0], b, best);
+        if (e != cudaSuccess) rc = cuda_fail(e, "lbm_batch_autotune");
+    }
+    b->graph_valid = false;
+    if (rows) *rows = b->seg;
+    return rc;
+}
+
+int lbm_batch_step(lbm_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0 || nsteps % b->K) return LBM_EINVAL;
+    if (!b->graph_valid) {
+        int rc = batch_capture(b);
+        if (rc) return rc;
+    }
+    for (int64_t done = 0; done < nsteps; done += b->K) {
+        CK(cudaGraphLaunch(b->graph, b->stream));
+        CK(cudaMemcpyAsync(b->h_results, b->d_results, 4 * (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        for (int c = 0; c < b->n; ++c) {
+            if (!b->active[c]) continue;
+            lbm_handle *h = b->h[c];
+            h->step += b->K;
+            h->launches += b->K;
+            b->steps[c] += b->K;
+            b->checks[c] += 1;
+            const double *r = b->h_results + 4 * c;
+            b->residual[c] = (b->checks[c] >= 2 && r[2] > 0.0) ? sqrt(r[1]) / ((double)b->K * sqrt(r[2])) : -1.0;
+            if (r[3] > 0.0) return LBM_EUNSTABLE;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int64_t *steps, int32_t *converged)
+{
+    if (!b || !(tol > 0.0) || max_steps < 0) return LBM_EINVAL;
+    int rc = LBM_OK;
+    int64_t done = 0;
+    for (;;) {
+        int n_active = 0;
+        for (int c = 0; c < b->n; ++c) n_active += b->active[c];
+        if (n_active == 0 || done + b->K > max_steps) break;
+        rc = lbm_batch_step(b, b->K);
+        if (rc) break;
+        done += b->K;
+        bool changed = false;
+        for (int c = 0; c < b->n; ++c)
+            if (b->active[c] && b->residual[c] >= 0.0 && b->residual[c] <= tol) {
+                b->active[c] = 0;
+                changed = true;
+            }
+        if (changed) CK(cudaMemcpyAsync(b->d_active, b->active.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    }
+    bool all = true;
+    for (int c = 0; c < b->n; ++c) {
+        const bool conv = b->residual[c] >= 0.0 && b->residual[c] <= tol;
+        if (steps) steps[c] = b->steps[c];
+        if (converged) converged[c] = conv ? 1 : 0;
+        all = all && conv;
+    }
+    if (rc) return rc;
+    return all ? LBM_OK : LBM_ETIMEOUT;
+}
+
+int lbm_batch_fields(lbm_batch *b, int32_t c, double *phi, double *u, double *v, double *T, double *dp)
+{
+    if (!b || c < 0 || c >= b->n) return LBM_EINVAL;
+    return lbm_fields(b->h[c], phi, u, v, T, dp);
+}
+
+int lbm_batch_diag(lbm_batch *b, int32_t c, double *residual, int64_t *steps)
+{
+    if (!b || c < 0 || c >= b->n) return LBM_EINVAL;
+    if (residual) *residual = b->residual[c];
+    if (steps) *steps = b->steps[c];
+    return LBM_OK;
+}
+
+int lbm_batch_init_fields(lbm_batch *b, int32_t c, const double *phi, const double *u, const double *v,
+                          const double *T, const double *dp)
+{
+    if (!b || c < 0 || c >= b->n) return LBM_EINVAL;
+    int rc = lbm_init_fields(b->h[c], phi, u, v, T, dp);
+    if (rc) return rc;
+    b->steps[c] = 0;
+    b->residual[c] = -1.0;
+    b->checks[c] = 0;
+    b->active[c] = 1;
+    CK(cudaMemcpyAsync(b->d_active, b->active.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+int lbm_batch_size(const lbm_batch *b, int32_t *n, int32_t *ctas, int32_t *rows)
+{
+    if (!b) return LBM_EINVAL;
+    if (n) *n = b->n;
+    if (ctas) *ctas = b->n_ctas;
+    if (rows) *rows = b->seg;
+    return LBM_OK;
 }
 
 }  // extern "C"

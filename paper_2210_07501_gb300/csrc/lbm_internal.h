@@ -13,6 +13,14 @@ namespace lbm {
 template <typename Real, typename Store, int QF, int QT>
 cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_rows);
 
+// Many cases in one launch (see batch_kernel): ctas[i] = (case, strip, segment, 0).
+template <typename Real, typename Store, int QF, int QT>
+cudaError_t launch_batch(const StepArgs<Real, Store> *cases, const int4 *ctas, int n_ctas, const int *active, int seg,
+                         cudaStream_t s);
+// Columns per strip of the step kernel, and CTAs of the batch kernel resident on the device.
+template <typename Real, typename Store, int QF, int QT> int step_strip_width();
+template <typename Real, typename Store, int QF, int QT> int resident_ctas();
+
 // Initialisation: macro [5][ny][nx] (phi, u, v, T, dp) holds the fields; entries whose
 // bit in `defaults` (1 phi, 2 u, 4 v, 8 T, 16 dp) is set are filled with the defaults
 // first.  Then the populations are set to the central-moment equilibria.

@@ -78,7 +78,7 @@ __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int
 }
 
 template <typename Real, typename Store, int QF, int QT, int TX>
-__global__ void __launch_bounds__(TX, 2) march_kernel(const StepArgs<Real, Store> A, int seg)
+__device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int seg, int bx, int by)
 {
     using R2 = typename Vec2<Real>::T;
     constexpr int PX = TX + 4, SX = TX + 2;
@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(TX, 2) march_kernel(const StepArgs<Real, Store
     const long long plane = A.plane;
     const Phys<Real> &P = A.P;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = blockIdx.y * seg;
+    const int x0 = bx * TX;
+    const int y0 = by * seg;
     const int y1 = min(y0 + seg, ny);
     const int x = x0 + tid;
     const bool xin = x < nx;
@@ -313,6 +313,53 @@ __global__ void __launch_bounds__(TX, 2) march_kernel(const StepArgs<Real, Store
     }
 }
 
+template <typename Real, typename Store, int QF, int QT, int TX>
+__global__ void __launch_bounds__(TX, 2) march_kernel(const StepArgs<Real, Store> A, int seg)
+{
+    march_body<Real, Store, QF, QT, TX>(A, seg, blockIdx.x, blockIdx.y);
+}
+
+// Many channels of uneven size in one launch: CTA i works on strip ctas[i].y, segment
+// ctas[i].z of case ctas[i].x, with that case's arguments; cases whose active flag is 0
+// (converged) are skipped.
+template <typename Real, typename Store, int QF, int QT, int TX>
+__global__ void __launch_bounds__(TX, 2) batch_kernel(const StepArgs<Real, Store> *__restrict__ cases,
+                                                       const int4 *__restrict__ ctas, const int *__restrict__ active,
+                                                       int seg)
+{
+    const int4 t = ctas[blockIdx.x];
+    if (!active[t.x]) return;
+    march_body<Real, Store, QF, QT, TX>(cases[t.x], seg, t.y, t.z);
+}
+
+template <typename Real> constexpr int march_width() { return std::is_same<Real, double>::value ? 128 : 256; }
+
+template <typename Real, typename Store, int QF, int QT>
+int step_strip_width()
+{
+    return march_width<Real>();
+}
+
+template <typename Real, typename Store, int QF, int QT>
+cudaError_t launch_batch(const StepArgs<Real, Store> *cases, const int4 *ctas, int n_ctas, const int *active, int seg,
+                         cudaStream_t s)
+{
+    constexpr int TX = march_width<Real>();
+    batch_kernel<Real, Store, QF, QT, TX><<<n_ctas, TX, 0, s>>>(cases, ctas, active, seg);
+    return cudaGetLastError();
+}
+
+template <typename Real, typename Store, int QF, int QT>
+int resident_ctas()
+{
+    constexpr int TX = march_width<Real>();
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<Real, Store, QF, QT, TX>, TX, 0);
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
 // Segment length: the grid (strips x segments) is made as close as possible to a whole
 // number of waves of resident CTAs, preferring long segments (each segment re-derives 4
 // rows of phi and 2 of sigma to start its window).
@@ -340,7 +387,7 @@ template <typename Real, typename Store, int QF, int QT>
 cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_rows)
 {
     // FP64 needs ~240 registers per thread: 128-thread strips; otherwise 256
-    constexpr int TX = std::is_same<Real, double>::value ? 128 : 256;
+    constexpr int TX = march_width<Real>();
     static int slots = 0;   // resident CTAs on the device (per template instance)
     if (slots == 0) {
         int dev = 0, sms = 0, per_sm = 0;
@@ -356,7 +403,12 @@ cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_
     return cudaGetLastError();
 }
 
-#define LBM_INST(R, S, QF, QT) template cudaError_t launch_step<R, S, QF, QT>(const StepArgs<R, S> &, cudaStream_t, int);
+#define LBM_INST(R, S, QF, QT)                                                                              \
+    template cudaError_t launch_step<R, S, QF, QT>(const StepArgs<R, S> &, cudaStream_t, int);             \
+    template cudaError_t launch_batch<R, S, QF, QT>(const StepArgs<R, S> *, const int4 *, int, const int *, \
+                                                    int, cudaStream_t);                                   \
+    template int step_strip_width<R, S, QF, QT>();                                                         \
+    template int resident_ctas<R, S, QF, QT>();
 LBM_INST(double, double, 5, 5)
 LBM_INST(double, double, 5, 9)
 LBM_INST(double, double, 9, 5)

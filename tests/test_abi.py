@@ -107,3 +107,18 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.lbm_fields(None, None, None, None, None, None) == pkg.LBM_EINVAL
     lib.lbm_destroy(None)
     assert lib.lbm_strerror(pkg.LBM_EIO) == b"checkpoint I/O error"
+
+
+def test_sweep_generator_matches_the_stated_distribution():
+    import lbm_workloads as WL
+    cases = WL.sweep_cases(96, seed=0)
+    assert len(cases) == 96
+    for c in cases:
+        d, p = c["domain"], c["params"]
+        assert d["nx"] in (256, 512, 1024) and d["ny"] in (64, 128, 256)
+        assert -2e-5 <= p["sigma1"] <= 2e-5 and -4e-4 <= p["sigma2"] <= 0.0
+        assert 0.5 <= p["cond_ratio"] <= 4.0 and 0.5 <= p["visc_ratio"] <= 4.0
+        ab = (d["ny"] - d["b"]) / d["b"]
+        assert 0.2 <= ab <= 4.5
+    assert WL.sweep_cases(96, seed=0) == cases            # seeded
+    assert len({(c["domain"]["nx"], c["domain"]["ny"]) for c in cases}) == 9
