@@ -323,6 +323,50 @@ def bench_gpu(args):
     return 0
 
 
+def bench_sweep(args):
+    """Batched uneven sweep against the plain per-case solver: wall time to steady state
+    (residual <= tol) for the first `args.sweep` channels of the seeded 96-channel sweep."""
+    import torch
+
+    import paper_2210_07501_gb300 as pkg
+    pkg.build()
+    pkg.load()
+    cases = WL.sweep_cases(96, seed=0)[:args.sweep]
+    K = 100
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = pkg.LbmBatch(cases, precision="fp32")
+    b.lbm_batch_set_check_interval(K)
+    rows = b.lbm_batch_autotune(5)
+    steps_b, conv_b = b.lbm_batch_run_to_steady(args.sweep_tol, args.sweep_max)
+    t_batch = time.perf_counter() - t0
+    size = b.lbm_batch_size()
+    b.close()
+    t0 = time.perf_counter()
+    steps_s, conv_s = [], []
+    for w in cases:
+        g = pkg.Lbm(w["domain"], w["params"], precision="fp32")
+        g.lbm_set_check_interval(K)
+        g.lbm_autotune(3)
+        ok, n = g.lbm_run_to_steady(args.sweep_tol, args.sweep_max)
+        steps_s.append(n)
+        conv_s.append(ok)
+        g.close()
+    t_single = time.perf_counter() - t0
+    sites = [w["domain"]["nx"] * w["domain"]["ny"] for w in cases]
+    lu = sum(s * n for s, n in zip(sites, steps_b))
+    line = {"sweep": {
+        "cases": len(cases), "generator": "seeded sweep_cases(96, seed=0), first cases", "precision": "fp32",
+        "tol": args.sweep_tol, "max_steps": args.sweep_max, "check_interval": K,
+        "batched_s": t_batch, "per_case_s": t_single, "speedup": t_single / t_batch,
+        "converged_batched": int(sum(conv_b)), "converged_per_case": int(sum(conv_s)),
+        "same_steps": steps_b == steps_s, "batched_mlups": lu / t_batch / 1e6,
+        "batch_ctas": size["ctas"], "segment_rows": rows,
+        "steps": steps_b, "sites_total": sum(sites)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,11 +378,16 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--ny", type=int, default=0, help="rows of a shorter channel (profiling); 0 = full")
     ap.add_argument("--segment", type=int, default=0, help="rows per CTA segment; 0 = autotune")
+    ap.add_argument("--sweep", type=int, default=0, help="run the batched-sweep comparison on N channels")
+    ap.add_argument("--sweep-tol", type=float, default=1e-5)
+    ap.add_argument("--sweep-max", type=int, default=60000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return bench_reference(args)
+    if args.sweep:
+        return bench_sweep(args)
     return bench_gpu(args)
 
 
