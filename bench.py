@@ -367,6 +367,22 @@ def bench_sweep(args):
     return 0
 
 
+def bench_warmstart(args):
+    """Learned warm start: surrogate trained on solver-generated steady channels (256 x 64),
+    then warm vs cold starts on held-out seeds."""
+    import paper_2210_07501_gb300 as pkg
+    from paper_2210_07501_gb300 import warmstart
+    pkg.build()
+    pkg.load()
+    n_train, n_test = args.warmstart
+    train = WL.surrogate_cases(n_train, seed=1000)
+    test = WL.surrogate_cases(n_test, seed=2000)
+    r = warmstart.experiment(train, test, tol=args.sweep_tol, max_steps=args.sweep_max, iters=args.train_iters,
+                             batch=16, lr=1e-3, seed=0)
+    print(json.dumps({"warmstart": r}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,6 +397,9 @@ def main(argv=None):
     ap.add_argument("--sweep", type=int, default=0, help="run the batched-sweep comparison on N channels")
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)
+    ap.add_argument("--warmstart", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
+                    help="learned warm start: train on TRAIN channels, compare on TEST channels")
+    ap.add_argument("--train-iters", type=int, default=3000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -388,6 +407,8 @@ def main(argv=None):
         return bench_reference(args)
     if args.sweep:
         return bench_sweep(args)
+    if args.warmstart:
+        return bench_warmstart(args)
     return bench_gpu(args)
 
 

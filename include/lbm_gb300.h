@@ -219,6 +219,30 @@ int lbm_batch_init_fields(lbm_batch *b, int32_t c, const double *phi, const doub
 int lbm_batch_size(const lbm_batch *b, int32_t *n, int32_t *ctas, int32_t *rows);
 void lbm_batch_destroy(lbm_batch *b);
 
+/* ---- learned warm start: a small convolutional surrogate of the steady fields ----
+ * Not a step of the paper's method: it predicts the steady phi, u, v, T of a channel from
+ * its parameters and heating profile, and its prediction initialises the LB solver
+ * (lbm_init_fields), which then converges to the LB solution and judges the error.
+ * Network: six 3x3 convolutions, channels 9 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, SiLU between
+ * layers, periodic in x, zero padding in y; FP32 weights, activations stored in BF16
+ * (bf16_activations != 0) or FP32, FP32 accumulation.  Parameters, in order per layer:
+ * weights [Cout][Cin][3][3], then biases [Cout].  Inputs x [B][9][H][W] and outputs /
+ * targets [B][4][H][W] are caller-owned FP32 device arrays.  Deterministic. */
+typedef struct lbm_cnn lbm_cnn;
+int lbm_cnn_create(int32_t H, int32_t W, int32_t batch_max, int32_t bf16_activations, uint64_t seed, void *stream,
+                   lbm_cnn **out);
+int lbm_cnn_num_params(const lbm_cnn *c, int64_t *n);
+int lbm_cnn_get_params(lbm_cnn *c, float *host);             /* host array of num_params floats */
+int lbm_cnn_set_params(lbm_cnn *c, const float *host);       /* also resets the optimiser state */
+int lbm_cnn_forward(lbm_cnn *c, const float *x, int32_t B, float *y);
+/* Forward + backward of the mean squared error over all outputs: *loss (may be NULL) and
+ * the gradient with respect to every parameter (grad_host, may be NULL).  Synchronises. */
+int lbm_cnn_gradients(lbm_cnn *c, const float *x, const float *target, int32_t B, float *grad_host, double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error. */
+int lbm_cnn_train_step(lbm_cnn *c, const float *x, const float *target, int32_t B, float lr, double *loss);
+const char *lbm_cnn_strerror(void);
+void lbm_cnn_destroy(lbm_cnn *c);
+
 /* Release the handle and its device memory; NULL-safe. */
 void lbm_destroy(lbm_handle *h);
 

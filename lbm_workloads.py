@@ -127,3 +127,21 @@ def sweep_cases(n_cases: int = 96, seed: int = 0) -> list:
                                                    q_phi=5, q_T=5),
                         sigma1=s1, sigma2=s2, cond_ratio=kr, visc_ratio=mr))
     return out
+
+
+def surrogate_cases(n_cases: int, seed: int, nx: int = 256, ny: int = 64) -> list:
+    """The sweep's parameter distribution on one fixed grid (the warm-start surrogate's
+    training and test channels; 256 x 64 by default): sigma1 ~ U[-2e-5, 2e-5],
+    sigma2 ~ U[-4e-4, 0], a/b ~ U[0.25, 4], k~ ~ U[0.5, 4], mu~ ~ U[0.5, 4], W = 5, tau = 0.8."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_cases):
+        s1 = float(rng.uniform(-2e-5, 2e-5))
+        s2 = float(rng.uniform(-4e-4, 0.0))
+        ab = float(rng.uniform(0.25, 4.0))
+        kr = float(rng.uniform(0.5, 4.0))
+        mr = float(rng.uniform(0.5, 4.0))
+        b = float(min(max(round(ny / (1.0 + ab)), 3), ny - 3))
+        out.append(_cfg(f"surrogate-{seed}-{i}", dict(nx=nx, ny=ny, b=b, W=5.0, heat_periods=1, q_phi=5, q_T=5),
+                        sigma1=s1, sigma2=s2, cond_ratio=kr, visc_ratio=mr))
+    return out

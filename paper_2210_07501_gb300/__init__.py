@@ -85,6 +85,17 @@ SIGNATURES = {
     "lbm_batch_size": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     "lbm_batch_destroy": (None, [_H]),
+    "lbm_cnn_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.c_void_p, ctypes.POINTER(_H)]),
+    "lbm_cnn_num_params": (ctypes.c_int, [_H, _I64P]),
+    "lbm_cnn_get_params": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_cnn_set_params": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_cnn_forward": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "lbm_cnn_gradients": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_float), _D]),
+    "lbm_cnn_train_step": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, _D]),
+    "lbm_cnn_strerror": (ctypes.c_char_p, []),
+    "lbm_cnn_destroy": (None, [_H]),
     "lbm_destroy": (None, [_H]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -127,6 +138,19 @@ def _field(a, shape):
     return np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
 
 
+_CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream as an explicit handle
+
+
+def stream_handle(stream):
+    """ctypes value for a stream argument: None (the library makes its own stream), an int,
+    or a torch.cuda.Stream.  Torch's default stream has handle 0, which the C ABI would read
+    as "none given", so it is passed as cudaStreamLegacy to keep the caller's ordering."""
+    if stream is None:
+        return None
+    h = stream if isinstance(stream, int) else stream.cuda_stream
+    return ctypes.c_void_p(h if h else _CUDA_STREAM_LEGACY)
+
+
 def make_domain(domain: dict, precision="fp64") -> LbmDomain:
     d = LbmDomain()
     for k in ("nx", "ny", "heat_periods", "q_phi", "q_T"):
@@ -155,9 +179,7 @@ class Lbm:
         self.q_phi, self.q_T = int(domain["q_phi"]), int(domain["q_T"])
         self.precision = precision
         self._h = _H()
-        s = None
-        if stream is not None:
-            s = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        s = stream_handle(stream)
         self._dom = make_domain(domain, precision)
         self._prm = make_params(params)
         _check(self._lib.lbm_create(ctypes.byref(self._dom), ctypes.byref(self._prm), s, ctypes.byref(self._h)),
@@ -275,9 +297,7 @@ class LbmBatch:
         self.n = n
         self.shapes = [(int(w["domain"]["ny"]), int(w["domain"]["nx"])) for w in workloads]
         self._h = _H()
-        s = None
-        if stream is not None:
-            s = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        s = stream_handle(stream)
         _check(self._lib.lbm_batch_create(n, doms, prms, s, ctypes.byref(self._h)), "lbm_batch_create")
 
     def lbm_batch_destroy(self):
@@ -333,3 +353,65 @@ class LbmBatch:
         n, c, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(self._lib.lbm_batch_size(self._h, ctypes.byref(n), ctypes.byref(c), ctypes.byref(r)), "lbm_batch_size")
         return {"cases": n.value, "ctas": c.value, "rows": r.value}
+
+
+class Cnn:
+    """The warm-start surrogate (one lbm_cnn).  x, y, target: float32 CUDA tensors.
+
+    The kernels run on `stream` (default: torch's current stream), so that tensors made by
+    torch on that stream are ready when the kernels read them and the outputs are ready
+    for torch's next operation on it."""
+
+    def __init__(self, H: int, W: int, batch_max: int, bf16: bool = True, seed: int = 0, stream=None):
+        self._lib = load()
+        self.H, self.W = int(H), int(W)
+        self._h = _H()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        s = stream_handle(stream)
+        _check(self._lib.lbm_cnn_create(self.H, self.W, int(batch_max), int(bool(bf16)), int(seed), s,
+                                        ctypes.byref(self._h)), "lbm_cnn_create")
+        n = ctypes.c_int64()
+        _check(self._lib.lbm_cnn_num_params(self._h, ctypes.byref(n)), "lbm_cnn_num_params")
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lbm_cnn_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self._lib.lbm_cnn_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "lbm_cnn_get_params")
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._lib.lbm_cnn_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "lbm_cnn_set_params")
+
+    def forward(self, x, y):
+        _check(self._lib.lbm_cnn_forward(self._h, ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                         ctypes.c_void_p(y.data_ptr())), "lbm_cnn_forward")
+
+    def gradients(self, x, target):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self._lib.lbm_cnn_gradients(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                           int(x.shape[0]), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           ctypes.byref(loss)), "lbm_cnn_gradients")
+        return g, loss.value
+
+    def train_step(self, x, target, lr: float) -> float:
+        loss = ctypes.c_double()
+        _check(self._lib.lbm_cnn_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                            int(x.shape[0]), float(lr), ctypes.byref(loss)), "lbm_cnn_train_step")
+        return loss.value

@@ -1,0 +1,33 @@
+"""The learned warm start gains over the plain cold start: a surrogate trained (with the
+library's own kernels) on steady channels produced by the batched solver, then used to
+initialise held-out channels, which reach the tolerance in fewer steps and converge to the
+same LB solution as the cold start (the judge of the surrogate's error)."""
+import numpy as np
+import pytest
+
+import lbm_workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_gains_over_cold_start():
+    pytest.importorskip("torch")
+    import paper_2210_07501_gb300 as pkg
+    from paper_2210_07501_gb300 import warmstart
+    pkg.build()
+    pkg.load()
+    train = WL.surrogate_cases(96, seed=11, nx=64, ny=32)
+    test = WL.surrogate_cases(8, seed=12, nx=64, ny=32)
+    r = warmstart.experiment(train, test, tol=1e-5, max_steps=20000, iters=1500, batch=16, lr=2e-3)
+    print(r)
+    assert r["loss_last"] < 0.05 * r["loss_first"]
+    assert r["both_converged"] >= 4
+    # never slower by more than one check interval, faster on average
+    assert all(w <= c + 100 for w, c in zip(r["warm_steps"], r["cold_steps"]))
+    assert r["warm_steps_mean_converged"] < r["cold_steps_mean_converged"]
+    assert r["warm_fewer_steps_cases"] >= 4
+    # the surrogate alone is a rough but useful guess; the LB corrects it
+    assert r["surrogate_rel_l2_vs_lb"]["phi"] < 0.1 and r["surrogate_rel_l2_vs_lb"]["T"] < 0.3
+    # warm- and cold-started runs converge to the same LB solution
+    assert r["warm_vs_cold_final_rel_l2"]["phi"] < 1e-3
+    assert r["warm_vs_cold_final_rel_l2"]["T"] < 1e-3
