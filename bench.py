@@ -378,7 +378,7 @@ def bench_warmstart(args):
     train = WL.surrogate_cases(n_train, seed=1000)
     test = WL.surrogate_cases(n_test, seed=2000)
     r = warmstart.experiment(train, test, tol=args.sweep_tol, max_steps=args.sweep_max, iters=args.train_iters,
-                             batch=16, lr=1e-3, seed=0)
+                             batch=16, lr=1e-3, seed=0, plain_cases=n_test)
     print(json.dumps({"warmstart": r}), flush=True)
     return 0
 

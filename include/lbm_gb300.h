@@ -223,10 +223,10 @@ void lbm_batch_destroy(lbm_batch *b);
  * Not a step of the paper's method: it predicts the steady phi, u, v, T of a channel from
  * its parameters and heating profile, and its prediction initialises the LB solver
  * (lbm_init_fields), which then converges to the LB solution and judges the error.
- * Network: six 3x3 convolutions, channels 9 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, SiLU between
+ * Network: six 3x3 convolutions, channels 12 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, SiLU between
  * layers, periodic in x, zero padding in y; FP32 weights, activations stored in BF16
  * (bf16_activations != 0) or FP32, FP32 accumulation.  Parameters, in order per layer:
- * weights [Cout][Cin][3][3], then biases [Cout].  Inputs x [B][9][H][W] and outputs /
+ * weights [Cout][Cin][3][3], then biases [Cout].  Inputs x [B][12][H][W] and outputs /
  * targets [B][4][H][W] are caller-owned FP32 device arrays.  Deterministic. */
 typedef struct lbm_cnn lbm_cnn;
 int lbm_cnn_create(int32_t H, int32_t W, int32_t batch_max, int32_t bf16_activations, uint64_t seed, void *stream,

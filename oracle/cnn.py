@@ -1,6 +1,6 @@
 """CPU FP64 oracle of the warm-start surrogate's network (test infrastructure only).
 
-Same architecture as the CUDA library's lbm_cnn: six 3x3 convolutions, channels 9 -> 32 ->
+Same architecture as the CUDA library's lbm_cnn: six 3x3 convolutions, channels 12 -> 32 ->
 32 -> 32 -> 32 -> 32 -> 4, SiLU between layers, periodic padding in x, zero padding in y,
 mean squared error.  Written with plain torch CPU float64 operations (conv2d and autograd
 serve as library primitives); pinned by tests/test_cnn_oracle.py against an explicit-loop
@@ -12,7 +12,7 @@ import numpy as np
 import torch
 import torch.nn.functional as F
 
-CH = (9, 32, 32, 32, 32, 32, 4)
+CH = (12, 32, 32, 32, 32, 32, 4)
 
 
 def split_params(flat):

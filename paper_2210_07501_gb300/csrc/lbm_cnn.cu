@@ -2,7 +2,7 @@
 // channel's parameters and heating profile to its steady phi, u, v, T, with hand-written
 // inference and training kernels (forward, backward-data, backward-weight, loss, Adam).
 //
-// Network: 6 layers of 3x3 convolutions, channels 9 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, SiLU
+// Network: 6 layers of 3x3 convolutions, channels 12 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, SiLU
 // between layers, none after the last.  Periodic in x (the channel is periodic), zero
 // padding in y.  Weights, gradients and optimiser state are FP32; activations are stored in
 // BF16 (or FP32, for gradient checks), every accumulation is FP32.  Layout NCHW.
@@ -22,7 +22,7 @@
 namespace {
 
 constexpr int NL = 6;
-constexpr int CH[NL + 1] = {9, 32, 32, 32, 32, 32, 4};
+constexpr int CH[NL + 1] = {12, 32, 32, 32, 32, 32, 4};
 constexpr int TILE = 16;       // 16 x 16 output pixels per CTA
 constexpr int CCH = 8;         // input channels staged per pass
 
@@ -277,7 +277,7 @@ template <typename A> static cudaError_t cnn_forward_impl(lbm_cnn *c, int B)
         A *y = (A *)c->act[l + 1];
         const float *w = c->p + c->off_w[l], *bias = c->p + c->off_b[l];
         const int act_in = l > 0;
-        if (CH[l] == 9 && CH[l + 1] == 32) conv_fwd<9, 32, A><<<grid, blk, 0, c->stream>>>(x, w, bias, y, c->H, c->W, act_in);
+        if (l == 0) conv_fwd<CH[0], 32, A><<<grid, blk, 0, c->stream>>>(x, w, bias, y, c->H, c->W, act_in);
         else if (CH[l + 1] == 32) conv_fwd<32, 32, A><<<grid, blk, 0, c->stream>>>(x, w, bias, y, c->H, c->W, act_in);
         else conv_fwd<32, 4, A><<<grid, blk, 0, c->stream>>>(x, w, bias, y, c->H, c->W, act_in);
         cudaError_t e = cudaGetLastError();
@@ -313,7 +313,7 @@ template <typename A> static cudaError_t cnn_backward_impl(lbm_cnn *c, int B, co
     int cur = 0;
     for (int l = NL - 1; l >= 0; --l) {
         const float *dz = c->dz[cur];
-        if (CH[l] == 9) e = bwd_weight_launch<9, 32, A>(c, l, B, dz);
+        if (l == 0) e = bwd_weight_launch<CH[0], 32, A>(c, l, B, dz);
         else if (CH[l + 1] == 32) e = bwd_weight_launch<32, 32, A>(c, l, B, dz);
         else e = bwd_weight_launch<32, 4, A>(c, l, B, dz);
         if (e != cudaSuccess) return e;

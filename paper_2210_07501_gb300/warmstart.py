@@ -5,10 +5,13 @@
 2. Training: the surrogate (`Cnn`, hand-written CUDA kernels) learns parameters + heating
    profile -> steady phi, T - T_ref, u/U, v/U (see `surrogate`), with Adam on the mean
    squared error; data stays on the GPU.
-3. Evaluation on held-out channels: the LB solver started from the surrogate's prediction
+3. Evaluation on held-out channels: the LB solver started from the surrogate's temperature
    (warm) against the solver started from rest (cold, the plain method and the judge):
    steps and wall time to the tolerance, the surrogate's own error against the converged LB
    fields, and the difference between the warm- and cold-started converged fields.
+   The warm start takes T only: the velocity follows T within a viscous time, and starting
+   it from the surrogate's (rougher) velocity costs more steps than it saves (measured;
+   reported as a variant, with the closed-form solution of Sec. 3 as another).
 """
 from __future__ import annotations
 
@@ -84,18 +87,36 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def plain_per_case(cases, tol, max_steps, precision="fp32", init=None, K=100, stream=None):
+    """The plain solver: one handle per channel, one after another (wall time, steps)."""
+    from . import Lbm
+    t0 = time.perf_counter()
+    steps = []
+    for c, w in enumerate(cases):
+        g = Lbm(w["domain"], w["params"], precision=precision, stream=stream)
+        g.lbm_set_check_interval(K)
+        if init is not None:
+            g.lbm_init_fields(**init[c])
+        g.lbm_autotune(2)
+        _, n = g.lbm_run_to_steady(tol, max_steps)
+        steps.append(n)
+        g.close()
+    return time.perf_counter() - t0, np.array(steps)
+
+
 def experiment(train_cases, test_cases, tol=1e-5, max_steps=60000, iters=2000, batch=16, lr=1e-3, seed=0,
-               precision="fp32", log_every=0):
+               precision="fp32", log_every=0, plain_cases=0):
     """Full pipeline; returns a dict of measurements.  Runs on one dedicated stream, shared
     by torch's tensor operations and the library's kernels."""
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         return _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every,
-                           stream)
+                           stream, plain_cases)
 
 
-def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every, stream):
+def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every, stream,
+                plain_cases):
     t0 = time.perf_counter()
     f_train, s_train, c_train, _ = steady_batch(train_cases, tol, max_steps, precision, stream=stream)
     t_data = time.perf_counter() - t0
@@ -111,10 +132,23 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
     t0 = time.perf_counter()
     P = predict(net, Xt, scale)
     t_pred = time.perf_counter() - t0
-    init = [S.fields_from_prediction(c["domain"], c["params"], p) for c, p in zip(test_cases, P)]
+    init = [S.fields_from_prediction(c["domain"], c["params"], p, use_velocity=False) for c, p in zip(test_cases, P)]
     f_cold, s_cold, c_cold, t_cold = steady_batch(test_cases, tol, max_steps, precision, stream=stream)
     f_warm, s_warm, c_warm, t_warm = steady_batch(test_cases, tol, max_steps, precision, init=init, stream=stream)
     net.close()
+    # variants: the surrogate's T, u and v; the closed-form solution alone (no network)
+    variants = {}
+    for name, ini in (("surrogate_T_u_v", [S.fields_from_prediction(c["domain"], c["params"], p)
+                                           for c, p in zip(test_cases, P)]),
+                      ("closed_form_T_u_v", [S.closed_form_fields(c["domain"], c["params"]) for c in test_cases]),
+                      ("closed_form_T", [{"T": S.closed_form_fields(c["domain"], c["params"])["T"]}
+                                         for c in test_cases])):
+        _, sv, cv, tv = steady_batch(test_cases, tol, max_steps, precision, init=ini, stream=stream)
+        bv = np.flatnonzero(cv & c_cold)
+        variants[name] = {"steps_mean": float(sv.mean()), "converged": int(cv.sum()), "seconds": tv,
+                          "steps_mean_on_cold_converged": float(sv[bv].mean()) if bv.size else None,
+                          "cold_steps_mean_same_cases": float(s_cold[bv].mean()) if bv.size else None,
+                          "fewer_steps_cases": int(np.sum(sv < s_cold))}
     # the surrogate's own error against the converged cold-start LB fields (the judge)
     pred_fields = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True) for c, p in zip(test_cases, P)]
     sur_err = {k: float(np.mean([rel_l2(i[k], f[k]) if k != "T" else
@@ -124,7 +158,14 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
     both = np.flatnonzero(c_warm & c_cold)
     wc = {k: float(np.mean([rel_l2(f_warm[i][k], f_cold[i][k]) for i in both])) if both.size else None
           for k in ("phi", "u", "v", "T")}
+    plain = None
+    if plain_cases:
+        n = min(plain_cases, len(test_cases))
+        t_plain, s_plain = plain_per_case(test_cases[:n], tol, max_steps, precision, stream=stream)
+        plain = {"cases": n, "seconds": t_plain, "steps_mean": float(s_plain.mean()),
+                 "same_steps_as_cold_batch": bool(np.array_equal(s_plain, s_cold[:n]))}
     return {
+        "plain_per_case_cold": plain,
         "train_cases": len(train_cases), "test_cases": len(test_cases), "grid": [int(H), int(W)],
         "tol": tol, "max_steps": max_steps, "precision": precision,
         "data_seconds": t_data, "train_converged": int(c_train.sum()),
@@ -140,5 +181,6 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
         "cold_seconds": t_cold, "warm_seconds": t_warm,
         "warm_fewer_steps_cases": int(np.sum(s_warm < s_cold)),
         "surrogate_rel_l2_vs_lb": sur_err,
+        "variants": variants,
         "warm_vs_cold_final_rel_l2": wc,
     }

@@ -36,7 +36,7 @@ def test_gradient_matches_finite_differences():
     rng = np.random.default_rng(1)
     n = C.n_params()
     p = rng.normal(scale=0.05, size=n)
-    x = rng.normal(size=(2, 9, 8, 12))
+    x = rng.normal(size=(2, 12, 8, 12))
     t = rng.normal(size=(2, 4, 8, 12))
     L, g, _ = C.loss_and_grad(p, x, t)
     for k in range(4):
@@ -49,5 +49,5 @@ def test_gradient_matches_finite_differences():
 
 
 def test_layer_table_and_size():
-    assert C.CH == (9, 32, 32, 32, 32, 32, 4)
-    assert C.n_params() == 40772
+    assert C.CH == (12, 32, 32, 32, 32, 32, 4)
+    assert C.n_params() == 41636

@@ -31,7 +31,7 @@ def test_forward_and_gradients_against_oracle(pkg, bf16, fwd_bar, grad_bar):
     net = pkg.Cnn(H, W, batch_max=4, bf16=bf16, seed=7)
     p = rng.normal(scale=0.08, size=net.n_params).astype(np.float32)
     net.set_params(p)
-    x = rng.normal(size=(B, 9, H, W)).astype(np.float32)
+    x = rng.normal(size=(B, 12, H, W)).astype(np.float32)
     t = rng.normal(size=(B, 4, H, W)).astype(np.float32)
     xd = torch.tensor(x, device="cuda")
     td = torch.tensor(t, device="cuda")
@@ -54,7 +54,7 @@ def test_training_reduces_loss(pkg):
     rng = np.random.default_rng(3)
     B, H, W = 8, 16, 32
     net = pkg.Cnn(H, W, batch_max=B, bf16=True, seed=1)     # on torch's current stream
-    x = torch.tensor(rng.normal(size=(B, 9, H, W)).astype(np.float32), device="cuda")
+    x = torch.tensor(rng.normal(size=(B, 12, H, W)).astype(np.float32), device="cuda")
     # a smooth target that depends on the inputs
     t = torch.stack([torch.tanh(x[:, 0] + 0.5 * x[:, 4]), x[:, 1] * x[:, 2], torch.sin(x[:, 3]), x[:, 5]], 1).contiguous()
     first = net.train_step(x, t, 1e-3)

@@ -22,12 +22,14 @@ def test_warm_start_gains_over_cold_start():
     print(r)
     assert r["loss_last"] < 0.05 * r["loss_first"]
     assert r["both_converged"] >= 4
-    # never slower by more than one check interval, faster on average
-    assert all(w <= c + 100 for w, c in zip(r["warm_steps"], r["cold_steps"]))
-    assert r["warm_steps_mean_converged"] < r["cold_steps_mean_converged"]
-    assert r["warm_fewer_steps_cases"] >= 4
-    # the surrogate alone is a rough but useful guess; the LB corrects it
-    assert r["surrogate_rel_l2_vs_lb"]["phi"] < 0.1 and r["surrogate_rel_l2_vs_lb"]["T"] < 0.3
+    # the warm start (surrogate T) is never slower and reaches the tolerance in fewer steps
+    # (on these short channels the thermal transient is short, so the gain is modest: ~7 %;
+    # on the 256 x 64 channels of the full experiment it is ~59 %)
+    assert all(w <= c for w, c in zip(r["warm_steps"], r["cold_steps"]))
+    assert r["warm_steps_mean_converged"] < 0.97 * r["cold_steps_mean_converged"]
+    assert r["warm_fewer_steps_cases"] >= 6
+    # the surrogate's temperature is close to the converged LB one (the judge)
+    assert r["surrogate_rel_l2_vs_lb"]["phi"] < 0.1 and r["surrogate_rel_l2_vs_lb"]["T"] < 0.05
     # warm- and cold-started runs converge to the same LB solution
     assert r["warm_vs_cold_final_rel_l2"]["phi"] < 1e-3
     assert r["warm_vs_cold_final_rel_l2"]["T"] < 1e-3
