@@ -306,7 +306,7 @@ def bench_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(),
                      "bytes_per_node": bpn, "peak_source": peak_kind,
-                     "kernel": "lbm::march_kernel<float,float,5,5,256> (+ reductions every 100 steps in the region)"},
+                     "kernel": "lbm::march_kernel<float,float,5,5,128> (+ reductions every 100 steps in the region)"},
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clocks,

@@ -47,6 +47,8 @@ extern "C" {
 #define LBM_EUNSTABLE (-4) /* a non-finite value appeared in the macroscopic fields  */
 #define LBM_ETIMEOUT (-5)  /* run_to_steady reached max_steps before the tolerance   */
 #define LBM_EIO (-6)       /* checkpoint file could not be read or written, or is bad */
+#define LBM_EDEVICE (-7)   /* a step kernel gave up waiting (~1 s) for its own shared- */
+                           /* memory copies; the state is invalid (never seen in use)  */
 
 /* ---- storage precision of the populations (arithmetic: FP64 for LBM_FP64, else FP32) ---- */
 #define LBM_FP64 0
@@ -138,6 +140,16 @@ int lbm_load(lbm_handle *h, const char *path);
  * (0 = automatic: chosen from the device's occupancy so the grid is a whole number of
  * waves).  Affects speed only, never the results. */
 int lbm_set_segment(lbm_handle *h, int32_t rows);
+
+/* Test hook for the fault path (not part of the method).  The step kernel stages its
+ * population rows in shared memory with asynchronous bulk copies and waits for them on
+ * mbarriers with a limit of about one second; after the limit it flags a fault and
+ * abandons the step instead of hanging.  With on != 0 every copy stage waits for 16 bytes
+ * more than it copies, so the waits run out: the next lbm_step returns at once, the next
+ * lbm_diag / lbm_fields (or batch step) returns LBM_EDEVICE after a few seconds, and the
+ * state is invalid until lbm_init_fields, lbm_set_state or lbm_load.  on = 0 restores
+ * normal stepping.  No GPU fault or trap is involved. */
+int lbm_test_stall_copies(lbm_handle *h, int32_t on);
 
 /* Autotuner: times `reps` launches of the step kernel for each candidate segment length
  * (automatic, 8 .. 256 rows below ny) and keeps the fastest; *rows (may be NULL) receives

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EIO = 0, -1, -2, -3, -4, -5, -6
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EIO, LBM_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 LBM_FP64, LBM_FP32, LBM_FP16 = 0, 1, 2
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16}
@@ -67,6 +67,7 @@ SIGNATURES = {
     "lbm_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
     "lbm_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
     "lbm_set_segment": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "lbm_test_stall_copies": (ctypes.c_int, [_H, ctypes.c_int32]),
     "lbm_autotune": (ctypes.c_int, [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "lbm_bytes_per_node": (ctypes.c_int, [_H, _I64P]),
     "lbm_launch_count": (ctypes.c_int, [_H, _I64P]),
@@ -260,6 +261,9 @@ class Lbm:
 
     def lbm_set_segment(self, rows: int):
         _check(self._lib.lbm_set_segment(self._h, int(rows)), "lbm_set_segment")
+
+    def lbm_test_stall_copies(self, on: bool):
+        _check(self._lib.lbm_test_stall_copies(self._h, int(bool(on))), "lbm_test_stall_copies")
 
     def lbm_autotune(self, reps: int = 20) -> int:
         r = ctypes.c_int32()

@@ -33,12 +33,13 @@ struct lbm_handle {
     double *macro;          // [5][ny][nx]
     double *uprev;          // [2][ny][nx]
     double *partials;       // reduction scratch [nblk][4]
-    double *result;         // [2][4]: last check, last diag
-    double *host_result;    // pinned [8]
+    double *result;         // [2][4]: last check, last diag; then the device fault word (8 bytes)
+    double *host_result;    // pinned [9]
     double *staging;        // lazily allocated [9][ny][nx] doubles for state I/O
     int cur;
     int64_t step, check_interval, launches;
     int seg_rows;           // rows per CTA segment of the step kernel (0 = automatic)
+    unsigned int tx_extra;  // lbm_test_stall_copies: extra bytes each copy stage waits for
     int64_t last_check_step, prev_check_step;
     bool have_check, have_prev_check;
     double res_du2, res_u2;
@@ -117,6 +118,8 @@ template <typename Real, typename Store> static StepArgs<Real, Store> make_args(
     A.isf = Real(1.0 / h->sf);
     A.isg = Real(1.0 / h->sg);
     A.ish = Real(1.0 / h->sh);
+    A.fault = (unsigned int *)(h->result + 8);
+    A.tx_extra = h->tx_extra;
     return A;
 }
 
@@ -219,6 +222,7 @@ const char *lbm_strerror(int status)
     case LBM_EUNSTABLE: return "non-finite value in the fields (unstable)";
     case LBM_ETIMEOUT: return "tolerance not reached within max_steps";
     case LBM_EIO: return "checkpoint I/O error";
+    case LBM_EDEVICE: return "a step kernel gave up waiting for its copies (state invalid)";
     default: return "unknown status";
     }
 }
@@ -230,6 +234,7 @@ static int reset_diag(lbm_handle *h)
     h->res_du2 = h->res_u2 = 0.0;
     const size_t N = (size_t)h->nx * h->ny;
     CK(cudaMemsetAsync(h->uprev, 0, 2 * N * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(h->result + 8, 0, sizeof(double), h->stream));   // a new state clears a fault
     return LBM_OK;
 }
 
@@ -274,14 +279,16 @@ int lbm_create(const lbm_domain *domain, const lbm_params *params, void *stream,
     ok = ok && cudaMalloc((void **)&h->macro, 5 * N * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->uprev, 2 * N * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->partials, (size_t)reduce_blocks() * 4 * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc((void **)&h->result, 8 * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMallocHost((void **)&h->host_result, 8 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->result, 9 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void **)&h->host_result, 9 * sizeof(double)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(h);
         delete h;
         return LBM_ENOMEM;
     }
+    cudaMemsetAsync(h->result, 0, 9 * sizeof(double), h->stream);
+    h->host_result[8] = 0.0;
     // padding columns are never read, but keep them defined
     for (int b = 0; b < 2; ++b) {
         for (int k = 0; k < 3; ++k) cudaMemsetAsync(h->pop[b][k], 0, (size_t)Q[k] * h->plane * h->esize, h->stream);
@@ -400,7 +407,9 @@ int lbm_fields(lbm_handle *h, double *phi, double *u, double *v, double *T, doub
     double *dst[5] = {phi, u, v, T, dp};
     for (int k = 0; k < 5; ++k)
         if (dst[k]) CK(cudaMemcpyAsync(dst[k], h->macro + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->host_result + 8, h->result + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (*(const unsigned int *)(h->host_result + 8)) return LBM_EDEVICE;
     return LBM_OK;
 }
 
@@ -421,9 +430,10 @@ int lbm_diag(lbm_handle *h, double *mass, double *residual, int64_t *step)
     // residual terms of the last check, then a fresh mass / finiteness reduction
     CK(cudaMemcpyAsync(h->host_result, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(launch_reduce(h->macro, h->uprev, N, 0, h->partials, reduce_blocks(), h->result + 4, h->stream));
-    CK(cudaMemcpyAsync(h->host_result + 4, h->result + 4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->host_result + 4, h->result + 4, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const double *r = h->host_result;
+    if (*(const unsigned int *)(r + 8)) return LBM_EDEVICE;
     if (mass) *mass = r[4];
     if (residual) {
         const int64_t K = h->last_check_step - h->prev_check_step;
@@ -642,6 +652,13 @@ int lbm_set_segment(lbm_handle *h, int32_t rows)
     return LBM_OK;
 }
 
+int lbm_test_stall_copies(lbm_handle *h, int32_t on)
+{
+    if (!h) return LBM_EINVAL;
+    h->tx_extra = on ? 16u : 0u;
+    return LBM_OK;
+}
+
 int lbm_autotune(lbm_handle *h, int32_t reps, int32_t *rows)
 {
     if (!h || reps < 1) return LBM_EINVAL;
@@ -718,7 +735,7 @@ struct lbm_batch {
     int n_ctas = 0, seg = 32;
     int *d_active = nullptr;
     std::vector<int> active;
-    double *d_results = nullptr;       // [n][4] reduction results of the last check
+    double *d_results = nullptr;       // [n][4] reduction results of the last check, then the fault word
     double *h_results = nullptr;       // pinned copy
     std::vector<int64_t> steps;        // steps taken per case
     std::vector<double> residual;      // last residual per case (-1 before two checks)
@@ -735,7 +752,10 @@ template <typename R, typename S, int QF, int QT> struct BatchArgsFn {
         std::vector<StepArgs<R, S>> a(b->n);
         for (int par = 0; par < 2; ++par)
             for (int m = 0; m < 2; ++m) {
-                for (int c = 0; c < b->n; ++c) a[c] = make_args<R, S>(b->h[c], par, m ? b->h[c]->macro : nullptr);
+                for (int c = 0; c < b->n; ++c) {
+                    a[c] = make_args<R, S>(b->h[c], par, m ? b->h[c]->macro : nullptr);
+                    a[c].fault = (unsigned int *)(b->d_results + 4 * (size_t)b->n);   // one word per batch
+                }
                 void *&dst = m ? b->d_args_m[par] : b->d_args[par];
                 if (!dst) {
                     cudaError_t e = cudaMalloc(&dst, sz * b->n);
@@ -863,10 +883,11 @@ int lbm_batch_create(int32_t n, const lbm_domain *domains, const lbm_params *par
     b->residual.assign(n, -1.0);
     b->checks.assign(n, 0);
     bool ok = cudaMalloc((void **)&b->d_active, n * sizeof(int)) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_results, 4 * (size_t)n * sizeof(double)) == cudaSuccess &&
-              cudaMallocHost((void **)&b->h_results, 4 * (size_t)n * sizeof(double)) == cudaSuccess;
+              cudaMalloc((void **)&b->d_results, (4 * (size_t)n + 1) * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_results, (4 * (size_t)n + 1) * sizeof(double)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); lbm_batch_destroy(b); return LBM_ENOMEM; }
     cudaError_t e = cudaMemcpy(b->d_active, b->active.data(), n * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_results, 0, (4 * (size_t)n + 1) * sizeof(double));
     if (e == cudaSuccess) e = dispatch<BatchArgsFn>(b->h[0], b);
     int slots = 0;
     if (e == cudaSuccess) e = dispatch<BatchSlotsFn>(b->h[0], &slots);
@@ -929,9 +950,10 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps)
     }
     for (int64_t done = 0; done < nsteps; done += b->K) {
         CK(cudaGraphLaunch(b->graph, b->stream));
-        CK(cudaMemcpyAsync(b->h_results, b->d_results, 4 * (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost,
-                           b->stream));
+        CK(cudaMemcpyAsync(b->h_results, b->d_results, (4 * (size_t)b->n + 1) * sizeof(double),
+                           cudaMemcpyDeviceToHost, b->stream));
         CK(cudaStreamSynchronize(b->stream));
+        if (*(const unsigned int *)(b->h_results + 4 * (size_t)b->n)) return LBM_EDEVICE;
         for (int c = 0; c < b->n; ++c) {
             if (!b->active[c]) continue;
             lbm_handle *h = b->h[c];

@@ -70,6 +70,8 @@ template <typename Real, typename Store> struct StepArgs {
     Phys<Real> P;
     Real sf, sg, sh;                // storage scales (value * s is stored); 1 unless FP16
     Real isf, isg, ish;
+    unsigned int *fault;            // set to nonzero by a CTA that abandoned the step
+    unsigned int tx_extra;          // bytes each stage expects beyond its copies: 0 (test hook)
 };
 
 // ---- storage conversion ----

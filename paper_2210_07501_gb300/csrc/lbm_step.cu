@@ -22,10 +22,10 @@ namespace lbm {
 // (sigma - sigma0, p - p0) and the unit normal (4 rows, radius-1 halo columns).  For output
 // row y the CTA adds phi of row y + 2 (from f pulled there, kept in registers until row y
 // collides), sigma and p of row y + 1 (from h pulled there, kept one row), the normals of
-// row y + 1, and then collides row y.  The loads for the next row are issued before the
-// current row's barriers and collisions (one-row software pipeline).  Every thread works
-// on the same row, so wall tests and row addresses are uniform across the CTA; only 4 halo
-// columns per strip are recomputed.
+// row y + 1, and then collides row y.  The population rows come from a ring of D stages
+// in shared memory filled by bulk copies D - 1 rows ahead (below); the first rows of a
+// segment are loaded directly.  Every thread works on the same row, so wall tests and row
+// addresses are uniform across the CTA; only 4 halo columns per strip are recomputed.
 template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
@@ -42,8 +42,15 @@ __device__ __forceinline__ void grad3_(const Real *rm, const Real *r0, const Rea
 template <typename Real>
 __device__ __forceinline__ Real rcp_(Real x)
 {
-    if constexpr (std::is_same<Real, double>::value) return 1.0 / x;
-    else return __frcp_rn(x);
+    if constexpr (std::is_same<Real, double>::value) {
+        return 1.0 / x;
+    } else {
+        // hardware reciprocal (about 1 ulp): the operands are densities and relaxation
+        // rates of order one, and FP32 storage dominates the error budget
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
 }
 
 // Loads of one row for the pull: populations of one lattice (plane base pointers `pl`,
@@ -77,159 +84,374 @@ __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int
     }
 }
 
+// ---- asynchronous row staging ----------------------------------------------------------
+// The population rows a CTA pulls from are copied into shared memory by the bulk-copy (TMA)
+// engine, D - 1 output rows ahead of the row being collided: the loads hold no registers
+// and each SM keeps several rows of every plane in flight.  Stage k of a CTA serves output
+// row y = y0 + k and holds the source rows of f pulled at row y + 2, of h pulled at y + 1
+// and of g pulled at y (after the wall rules: the reflected or reversed plane's row at a
+// wall), and dp of row y + 1, each over the strip's columns plus a halo on both sides.
+// Bulk copies move 16-byte aligned spans; columns that wrap around the periodic x edge, or
+// lie past the last 16-byte boundary of a row, are copied element by element by all threads
+// (cp.async, or plain loads for 2-byte values), and each thread then arrives on the slot's
+// mbarrier: a stage is complete when its mbarrier phase is, and every thread waits on it.
+__device__ __forceinline__ uint32_t smem_u32_(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init_(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32_(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence_() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx_(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32_(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32_(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32_(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32_(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the completion of the phase of `bar` with the given parity.  Gives up after
+// about one second (returns false): a copy that never lands must not hang the GPU.
+__device__ __forceinline__ bool mbar_wait_(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait_(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_();
+    while (!mbar_try_wait_(bar, parity))
+        if (globaltimer_() - t0 > 1000000000ull) return false;
+    return true;
+}
+// one element: cp.async (4 or 8 bytes), or a plain load and store
+template <bool ASYNC, typename T>
+__device__ __forceinline__ void cp_elem_(T *dst, const T *src)
+{
+    if constexpr (ASYNC && sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32_(dst)), "l"(src) : "memory");
+    else if constexpr (ASYNC && sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32_(dst)), "l"(src) : "memory");
+    else
+        *dst = *src;
+}
+// arrive on `bar` once this thread's earlier cp.async copies have landed (counted at init)
+__device__ __forceinline__ void cp_arrive_noinc_(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32_(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32_(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all_() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename Real, typename Store>
+__device__ __forceinline__ Real lds_(const Store *p)
+{
+    if constexpr (std::is_same<Store, __half>::value) return Real(__half2float(*p));
+    else return Real(*p);
+}
+
+#ifndef LBM_FP32_TX
+#define LBM_FP32_TX 128
+#endif
+// Columns per strip: 128 (FP32 and FP16 storage: four CTAs of 5 warps per SM; 256 runs 2 %
+// slower on the 8192 x 2048 channel); FP64 needs ~150-220 registers per thread, so 128 with
+// two CTAs per SM.
+template <typename Real> constexpr int march_width() { return std::is_same<Real, double>::value ? 128 : LBM_FP32_TX; }
+// Resident CTAs per SM the kernels are built for (registers and shared memory).
+template <typename Real> constexpr int march_ctas() { return march_width<Real>() == 128 && sizeof(Real) == 4 ? 4 : 2; }
+
+// Shared-memory geometry of the staging ring (host and device).
+template <typename Real, typename Store, int QF, int QT, int TX> struct StageGeo {
+    static constexpr int HS = sizeof(Store) == 2 ? 8 : 4;   // halo columns per side, population planes
+    static constexpr int HD = 4;                             // halo columns per side, dp plane
+    static constexpr int RS = TX + 2 * HS, RD = TX + 2 * HD; // staged row lengths (16-byte multiples)
+    static constexpr int NP = QF + QT + 9;                   // population planes per stage: f, h, g
+    static constexpr int BYTES = (NP * RS * (int)sizeof(Store) + RD * (int)sizeof(Real) + 127) / 128 * 128;
+    static constexpr int RINGS = 8 * (TX + 4) * (int)sizeof(Real) + 16 * (TX + 2) * (int)sizeof(Real);
+    // deepest ring that leaves room for march_ctas() CTAs per SM (228 KiB, 1 KiB reserved per CTA)
+    static constexpr int BUDGET = 233472 / march_ctas<Real>() - 1024 - 128 - 16 - RINGS;
+    static constexpr int D = (4 * BYTES + 128 <= BUDGET) ? 4 : ((3 * BYTES + 128 <= BUDGET) ? 3 : 2);
+    static constexpr int DYN = D * BYTES + 128;              // + one mbarrier per slot
+};
+
 template <typename Real, typename Store, int QF, int QT, int TX>
 __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int seg, int bx, int by)
 {
     using R2 = typename Vec2<Real>::T;
-    constexpr int PX = TX + 4, SX = TX + 2;
+    using G = StageGeo<Real, Store, QF, QT, TX>;
+    constexpr int PX = TX + 4, SX = TX + 2, NT = TX + 32;
+    constexpr int D = G::D, HS = G::HS, HD = G::HD, RS = G::RS, RD = G::RD, NP = G::NP;
+    constexpr int CS = 16 / (int)sizeof(Store), CD = 16 / (int)sizeof(Real);   // elements per 16 bytes
     __shared__ Real s_phi[8][PX];
     __shared__ R2 s_sp[4][SX];   // (sigma - sigma0, p - p0)
     __shared__ R2 s_n[4][SX];    // unit normal
+    __shared__ int s_abort;
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(s_dyn + D * G::BYTES);
 
     const int nx = A.nx, ny = A.ny, pitch = A.pitch;
-    const long long plane = A.plane;
     const Phys<Real> &P = A.P;
     const int tid = threadIdx.x;
     const int x0 = bx * TX;
     const int y0 = by * seg;
     const int y1 = min(y0 + seg, ny);
+    // Threads 0..TX-1 own the columns x0 + tid (phi, sigma, n, collision and store); the last
+    // warp (the edge warp) issues the bulk copies and computes the halo columns: lanes 0..3
+    // phi at x0-2, x0-1, x0+TX, x0+TX+1, lanes 0..1 sigma, p and n at x0-1, x0+TX.
+    const bool colt = tid < TX;
+    const int lane = tid - TX;
+    const bool doF = colt || lane < 4, doH = colt || lane < 2;
+    const int cf = colt ? tid : (lane < 2 ? lane - 2 : TX + lane - 2);   // column of phi, relative to x0
+    const int ch = colt ? tid : (lane == 0 ? -1 : TX);                   // column of sigma and n
     const int x = x0 + tid;
-    const bool xin = x < nx;
-    const int xw = wrap_(x, nx);
-    const int xm = xw == 0 ? nx - 1 : xw - 1, xp = xw == nx - 1 ? 0 : xw + 1;
-    const int hpc = tid < 2 ? tid : TX + tid;               // phi halo tile column (tid < 4)
-    const int hpx = wrap_(x0 - 2 + hpc, nx);
-    const int hpxm = hpx == 0 ? nx - 1 : hpx - 1, hpxp = hpx == nx - 1 ? 0 : hpx + 1;
-    const int hsc = tid == 0 ? 0 : TX + 1;                  // sigma/n halo tile column (tid < 2)
-    const int hsx = wrap_(x0 - 1 + hsc, nx);
-    const int hsxm = hsx == 0 ? nx - 1 : hsx - 1, hsxp = hsx == nx - 1 ? 0 : hsx + 1;
+    const bool xin = colt && x < nx;
+    const int xf = wrap_(x0 + cf, nx), xh = wrap_(x0 + ch, nx);
+    const int xfm = xf == 0 ? nx - 1 : xf - 1, xfp = xf == nx - 1 ? 0 : xf + 1;
+    const int xhm = xh == 0 ? nx - 1 : xh - 1, xhp = xh == nx - 1 ? 0 : xh + 1;
 
-    // Row inputs: f of the thread's column (for phi and the collision) and, on threads
-    // 0..3, f of one phi halo column; h and p of the thread's column and, on threads 0..1,
-    // of one sigma halo column.  All of them are loaded one row ahead of their use.
-    struct RowF {
-        Real f[QF], fh[QF];
+    // ---- staging geometry (CTA-uniform) ----
+    // staged column j of a population plane is global column sx0 + j (wrapped); the bulk
+    // part covers staged columns [boff, boff + bspan), the rest is copied element-wise
+    const int sx0 = x0 - HS, dx0 = x0 - HD;
+    const int blo = max(sx0, 0), bhi = min(x0 + TX + HS, nx / CS * CS);
+    const int bspan = bhi > blo ? bhi - blo : 0, boff = blo - sx0;
+    const int dlo = max(dx0, 0), dhi = min(x0 + TX + HD, nx / CD * CD);
+    const int dspan = dhi > dlo ? dhi - dlo : 0, doff = dlo - dx0;
+    const int nel_s = RS - bspan, nel_d = RD - dspan;          // element-wise columns per plane
+    const int n_edge = NP * nel_s + nel_d;
+    const bool edge = n_edge > 0;                               // then every thread arrives too
+    constexpr bool ASYNC = sizeof(Store) >= 4;
+    const uint32_t tx_bytes = uint32_t(NP * bspan * (int)sizeof(Store) + dspan * (int)sizeof(Real));
+    auto stage_pop = [&](int sl) { return reinterpret_cast<Store *>(s_dyn + sl * G::BYTES); };
+    auto stage_dp = [&](int sl) { return reinterpret_cast<Real *>(s_dyn + sl * G::BYTES + NP * RS * sizeof(Store)); };
+
+    // source row of staged plane p for output row yy: f pulled at yy + 3, h at yy + 1, g at yy
+    auto src_row = [&](int p, int yy) -> const Store * {
+        int a, r, kind;
+        const Store *base;
+        if (p < QF) {
+            a = p, r = yy + 3, kind = 0, base = A.f_in;
+        } else if (p < QF + QT) {
+            a = p - QF, r = yy + 1, kind = 2, base = A.h_in;
+        } else {
+            a = p - QF - QT, r = yy, kind = 1, base = A.g_in;
+        }
+        const int gy = mirror_row_(r, ny), ey = ey_(a);
+        const bool wall = (ey > 0 && gy == 0) || (ey < 0 && gy == ny - 1);
+        const int src = wall ? (kind == 0 ? mir_(a) : opp_(a)) : a;
+        return base + (long long)src * A.plane + (long long)(wall ? gy : gy - ey) * pitch;
     };
-    struct RowH {
-        Real h[QT], hh[QT], dp, dph;
-    };
-    auto load_f = [&](int r, RowF &q) {
-        const int gy = mirror_row_(r, ny);
-        pull_row_<0, QF>(A.fi, pitch, ny, nx, gy, xw, xm, xp, A.isf, A.twall, P.dTcold, q.f);
-        if (tid < 4) pull_row_<0, QF>(A.fi, pitch, ny, nx, gy, hpx, hpxm, hpxp, A.isf, A.twall, P.dTcold, q.fh);
-    };
-    auto load_h = [&](int r, RowH &q) {
-        const int gy = mirror_row_(r, ny);
-        pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, xw, xm, xp, A.ish, A.twall, P.dTcold, q.h);
-        q.dp = A.dp_in[gy * pitch + xw];
-        if (tid < 2) {
-            pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, hsx, hsxm, hsxp, A.ish, A.twall, P.dTcold, q.hh);
-            q.dph = A.dp_in[gy * pitch + hsx];
+    // Copies of stage `yy` into slot `sl` (every thread calls it; nothing past the segment).
+    auto issue = [&](int yy, int sl) {
+        if (yy >= y1) return;
+        Store *st = stage_pop(sl);
+        Real *sd = stage_dp(sl);
+        if (!colt) {
+            if (lane == 0) mbar_expect_tx_(&s_bar[sl], tx_bytes + A.tx_extra);
+            __syncwarp();
+            if (lane < NP) {
+                if (bspan > 0) bulk_g2s_(st + lane * RS + boff, src_row(lane, yy) + blo, bspan * sizeof(Store), &s_bar[sl]);
+            } else if (lane == NP) {
+                if (dspan > 0)
+                    bulk_g2s_(sd + doff, A.dp_in + (long long)mirror_row_(yy + 1, ny) * pitch + dlo,
+                              dspan * sizeof(Real), &s_bar[sl]);
+            }
+        }
+        if (edge) {
+            for (int e = tid; e < n_edge; e += NT) {
+                if (e < NP * nel_s) {
+                    const int p = e / nel_s, k = e - p * nel_s, j = k < boff ? k : k + bspan;
+                    cp_elem_<ASYNC>(st + p * RS + j, src_row(p, yy) + wrap_(sx0 + j, nx));
+                } else {
+                    const int k = e - NP * nel_s, j = k < doff ? k : k + dspan;
+                    cp_elem_<ASYNC>(sd + j, A.dp_in + (long long)mirror_row_(yy + 1, ny) * pitch + wrap_(dx0 + j, nx));
+                }
+            }
+            if constexpr (ASYNC) cp_arrive_noinc_(&s_bar[sl]);
+            else mbar_arrive_(&s_bar[sl]);
         }
     };
-    auto put_phi = [&](int r, const RowF &q) {
-        Real phi = q.f[0];
+    // Pulled values of a completed stage at the thread's columns (wall rules of Sec. 5.1).
+    auto read_f = [&](int sl, Real *f) {
+        const Store *st = stage_pop(sl) + HS + cf;
 #pragma unroll
-        for (int a = 1; a < QF; ++a) phi += q.f[a];
-        s_phi[r & 7][tid + 2] = phi;
-        if (tid < 4) {
-            Real ph = q.fh[0];
-#pragma unroll
-            for (int a = 1; a < QF; ++a) ph += q.fh[a];
-            s_phi[r & 7][hpc] = ph;
+        for (int a = 0; a < QF; ++a) {
+            // specular reflection keeps the x shift of the link
+            Real v = lds_<Real, Store>(st + a * RS - ex_(a));
+            if constexpr (scaled_<Store>()) v *= A.isf;
+            f[a] = v;
         }
     };
-    auto sig_of = [&](int r, Real dT, int col) -> Real {
-        if (r == -1) dT = Real(2) * A.twall[nx + col] - dT;   // T_ghost = 2 T_w - T_adjacent
+    // WALLS = false: rows away from the walls (no link of this row crosses one)
+    auto read_h = [&](auto walls, int sl, int r, Real *h, Real &dp) {
+        constexpr bool WALLS = decltype(walls)::value;
+        const Store *st = stage_pop(sl) + QF * RS + HS + ch;
+        const int gy = mirror_row_(r, ny);
+        const bool wb = WALLS && gy == 0, wt = WALLS && gy == ny - 1;
+#pragma unroll
+        for (int a = 0; a < QT; ++a) {
+            const int ex = ex_(a), ey = ey_(a);
+            const bool wall = (ey > 0 && wb) || (ey < 0 && wt);
+            Real v = lds_<Real, Store>(st + a * RS - (wall ? 0 : ex));
+            if constexpr (scaled_<Store>()) v *= A.ish;
+            if (wall) v = -v + Real(2.0 * w_<QT>(a)) * (ey > 0 ? A.twall[(1 - ex) * nx + xh] : P.dTcold);
+            h[a] = v;
+        }
+        dp = stage_dp(sl)[HD + ch];
+    };
+    auto read_g = [&](auto walls, int sl, int y, Real *g) {
+        constexpr bool WALLS = decltype(walls)::value;
+        const Store *st = stage_pop(sl) + (QF + QT) * RS + HS + tid;
+        const bool wb = WALLS && y == 0, wt = WALLS && y == ny - 1;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const int ey = ey_(a);
+            const bool wall = (ey > 0 && wb) || (ey < 0 && wt);
+            Real v = lds_<Real, Store>(st + a * RS - (wall ? 0 : ex_(a)));
+            if constexpr (scaled_<Store>()) v *= A.isg;
+            g[a] = v;
+        }
+    };
+    // Direct loads (first rows of a segment only).
+    auto load_f = [&](int r, Real *f) {
+        pull_row_<0, QF>(A.fi, pitch, ny, nx, mirror_row_(r, ny), xf, xfm, xfp, A.isf, A.twall, P.dTcold, f);
+    };
+    auto load_h = [&](int r, Real *h, Real &dp) {
+        const int gy = mirror_row_(r, ny);
+        pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, xh, xhm, xhp, A.ish, A.twall, P.dTcold, h);
+        dp = A.dp_in[gy * pitch + xh];
+    };
+    auto put_phi = [&](int r, const Real *f) {
+        Real phi = f[0];
+#pragma unroll
+        for (int a = 1; a < QF; ++a) phi += f[a];
+        s_phi[r & 7][cf + 2] = phi;
+    };
+    auto put_sig = [&](int r, const Real *h, Real dp) {
+        Real dT = h[0];
+#pragma unroll
+        for (int a = 1; a < QT; ++a) dT += h[a];
+        if (r == -1) dT = Real(2) * A.twall[nx + xh] - dT;   // T_ghost = 2 T_w - T_adjacent
         else if (r == ny) dT = Real(2) * P.dTcold - dT;
-        return dT * (P.sigma1 + P.sigma2 * dT);
-    };
-    auto put_sig = [&](int r, const RowH &q) {
-        Real dT = q.h[0];
-#pragma unroll
-        for (int a = 1; a < QT; ++a) dT += q.h[a];
         R2 v;
-        v.x = sig_of(r, dT, xw);
-        v.y = q.dp;
-        s_sp[r & 3][tid + 1] = v;
-        if (tid < 2) {
-            Real d = q.hh[0];
-#pragma unroll
-            for (int a = 1; a < QT; ++a) d += q.hh[a];
-            R2 w;
-            w.x = sig_of(r, d, hsx);
-            w.y = q.dph;
-            s_sp[r & 3][hsc] = w;
-        }
+        v.x = dT * (P.sigma1 + P.sigma2 * dT);
+        v.y = dp;
+        s_sp[r & 3][ch + 1] = v;
     };
     auto put_n = [&](int r) {
-        const Real *rm = s_phi[(r - 1) & 7], *r0 = s_phi[r & 7], *rp = s_phi[(r + 1) & 7];
         Real gx, gy;
         R2 n;
-        grad3_(rm, r0, rp, tid + 2, gx, gy);
+        grad3_(s_phi[(r - 1) & 7], s_phi[r & 7], s_phi[(r + 1) & 7], ch + 2, gx, gy);
         unit_normal_(gx, gy, P.g2min, n.x, n.y);
-        s_n[r & 3][tid + 1] = n;
-        if (tid < 2) {
-            grad3_(rm, r0, rp, hsc + 1, gx, gy);
-            unit_normal_(gx, gy, P.g2min, n.x, n.y);
-            s_n[r & 3][hsc] = n;
+        s_n[r & 3][ch + 1] = n;
+    };
+    // After a wait gave up: flag the fault, let every copy this CTA started land, return.
+    // (k_fail: the stage whose wait gave up; the later ones issued are waited for once more)
+    auto fail = [&](int k_fail, int k_last) {
+        cp_wait_all_();
+        if (tid == 0) {
+            if (A.fault) atomicOr(A.fault, 1u);
+            for (int k = k_fail + 1; k <= k_last; ++k) mbar_wait_(&s_bar[k % D], uint32_t((k / D) & 1));
         }
     };
 
-    // ---- prologue: phi rows y0-2 .. y0+1, sigma/p rows y0-1, y0, normals y0-1, y0 ----
-    Real fq0[QF], fq1[QF], hq0[QT], gn[9];
-    RowF fn;
-    RowH hn;
-    {
-        RowF t;
-        RowH th;
+    // ---- prologue: barriers; stages y0 .. y0+D-2 in flight; phi rows y0-2 .. y0+2,
+    // sigma/p rows y0-1, y0 and normals y0-1, y0 from direct loads ----
+    if (tid == 0) {
+        for (int k = 0; k < D; ++k) mbar_init_(&s_bar[k], edge ? NT + 1 : 1);
+        s_abort = 0;
+        mbar_init_fence_();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < D - 1; ++k) issue(y0 + k, k);
+    Real fq0[QF], fq1[QF], fq2[QF], hq0[QT];
+    if (doF) {
+        Real t[QF];
         load_f(y0 - 2, t);
         put_phi(y0 - 2, t);
         load_f(y0 - 1, t);
         put_phi(y0 - 1, t);
-        load_f(y0, t);
-        put_phi(y0, t);
-#pragma unroll
-        for (int a = 0; a < QF; ++a) fq0[a] = t.f[a];
-        load_f(y0 + 1, t);
-        put_phi(y0 + 1, t);
-#pragma unroll
-        for (int a = 0; a < QF; ++a) fq1[a] = t.f[a];
-        load_h(y0 - 1, th);
-        put_sig(y0 - 1, th);
-        load_h(y0, th);
-        put_sig(y0, th);
-#pragma unroll
-        for (int a = 0; a < QT; ++a) hq0[a] = th.h[a];
+        load_f(y0, fq0);
+        put_phi(y0, fq0);
+        load_f(y0 + 1, fq1);
+        put_phi(y0 + 1, fq1);
+        load_f(y0 + 2, fq2);
+        put_phi(y0 + 2, fq2);
     }
-    // next row's loads: f(y0+2), h(y0+1), g(y0)
-    load_f(y0 + 2, fn);
-    load_h(y0 + 1, hn);
-    pull_row_<1, 9>(A.gi, pitch, ny, nx, y0, xw, xm, xp, A.isg, A.twall, P.dTcold, gn);
+    if (doH) {
+        Real t[QT], dp;
+        load_h(y0 - 1, t, dp);
+        put_sig(y0 - 1, t, dp);
+        load_h(y0, hq0, dp);
+        put_sig(y0, hq0, dp);
+    }
     __syncthreads();
-    put_n(y0 - 1);
-    put_n(y0);
+    if (doH) {
+        put_n(y0 - 1);
+        put_n(y0);
+    }
 
     const Real c2 = Real(1.0 / 3.0), hf = Real(0.5);
+    int sl = 0;          // slot of the stage of row y
+    uint32_t par = 0;    // its mbarrier phase parity
+    // One barrier per row: before it, phi of row y + 3, sigma and p of row y + 1 and the
+    // normals of row y + 1 (from phi rows y .. y + 2, complete since the previous barrier);
+    // after it, row y collides.  The rings are deep enough that these writes never touch
+    // rows the previous row's collision may still be reading.
     for (int y = y0; y < y1; ++y) {
-        Real fq2[QF], hq1[QT], g[9];
-#pragma unroll
-        for (int a = 0; a < QF; ++a) fq2[a] = fn.f[a];
-#pragma unroll
-        for (int a = 0; a < QT; ++a) hq1[a] = hn.h[a];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) g[a] = gn[a];
-        put_phi(y + 2, fn);
-        put_sig(y + 1, hn);
-        // issue the loads of the next row before this row's barriers and collisions
-        if (y + 1 < y1) {
-            load_f(y + 3, fn);
-            load_h(y + 2, hn);
-            pull_row_<1, 9>(A.gi, pitch, ny, nx, y + 1, xw, xm, xp, A.isg, A.twall, P.dTcold, gn);
+        Real fq3[QF], hq1[QT], g[9];
+        if (!mbar_wait_(&s_bar[sl], par)) s_abort = 1;
+        if (doF) {
+            read_f(sl, fq3);
+            put_phi(y + 3, fq3);
+        }
+        if (y >= 1 && y <= ny - 3) {   // rows y and y + 1 are clear of the walls
+            if (doH) {
+                Real dp;
+                read_h(std::false_type(), sl, y + 1, hq1, dp);
+                put_sig(y + 1, hq1, dp);
+                put_n(y + 1);
+            }
+            if (colt) read_g(std::false_type(), sl, y, g);
+        } else {
+            if (doH) {
+                Real dp;
+                read_h(std::true_type(), sl, y + 1, hq1, dp);
+                put_sig(y + 1, hq1, dp);
+                put_n(y + 1);
+            }
+            if (colt) read_g(std::true_type(), sl, y, g);
+        }
+        // refill the slot read one row ago (every thread is past its reads) with row y + D - 1
+        issue(y + D - 1, sl == 0 ? D - 1 : sl - 1);
+        if (++sl == D) {
+            sl = 0;
+            par ^= 1u;
         }
         __syncthreads();
-        put_n(y + 1);
-        __syncthreads();
+        if (s_abort) {
+            fail(y - y0, min(y + D - 1, y1 - 1) - y0);
+            return;
+        }
         if (xin) {
             const int c = tid + 2, s = tid + 1;
             const Real *pm = s_phi[(y - 1) & 7], *p0 = s_phi[y & 7], *pp = s_phi[(y + 1) & 7];
@@ -307,6 +529,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         for (int a = 0; a < QF; ++a) {
             fq0[a] = fq1[a];
             fq1[a] = fq2[a];
+            fq2[a] = fq3[a];
         }
 #pragma unroll
         for (int a = 0; a < QT; ++a) hq0[a] = hq1[a];
@@ -314,7 +537,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
 }
 
 template <typename Real, typename Store, int QF, int QT, int TX>
-__global__ void __launch_bounds__(TX, 2) march_kernel(const StepArgs<Real, Store> A, int seg)
+__global__ void __launch_bounds__(TX + 32, march_ctas<Real>()) march_kernel(const StepArgs<Real, Store> A, int seg)
 {
     march_body<Real, Store, QF, QT, TX>(A, seg, blockIdx.x, blockIdx.y);
 }
@@ -323,7 +546,7 @@ __global__ void __launch_bounds__(TX, 2) march_kernel(const StepArgs<Real, Store
 // ctas[i].z of case ctas[i].x, with that case's arguments; cases whose active flag is 0
 // (converged) are skipped.
 template <typename Real, typename Store, int QF, int QT, int TX>
-__global__ void __launch_bounds__(TX, 2) batch_kernel(const StepArgs<Real, Store> *__restrict__ cases,
+__global__ void __launch_bounds__(TX + 32, march_ctas<Real>()) batch_kernel(const StepArgs<Real, Store> *__restrict__ cases,
                                                        const int4 *__restrict__ ctas, const int *__restrict__ active,
                                                        int seg)
 {
@@ -332,7 +555,6 @@ __global__ void __launch_bounds__(TX, 2) batch_kernel(const StepArgs<Real, Store
     march_body<Real, Store, QF, QT, TX>(cases[t.x], seg, t.y, t.z);
 }
 
-template <typename Real> constexpr int march_width() { return std::is_same<Real, double>::value ? 128 : 256; }
 
 template <typename Real, typename Store, int QF, int QT>
 int step_strip_width()
@@ -340,12 +562,33 @@ int step_strip_width()
     return march_width<Real>();
 }
 
+// Dynamic shared memory of the step kernels (the staging ring); the attribute that allows
+// it is set once per kernel instance, with the carveout at its shared-memory maximum.
+template <typename Real, typename Store, int QF, int QT>
+static int prepare_kernels()
+{
+    constexpr int TX = march_width<Real>();
+    constexpr int dyn = StageGeo<Real, Store, QF, QT, TX>::DYN;
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(march_kernel<Real, Store, QF, QT, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(batch_kernel<Real, Store, QF, QT, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(march_kernel<Real, Store, QF, QT, TX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100);
+        cudaFuncSetAttribute(batch_kernel<Real, Store, QF, QT, TX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100);
+        done = true;
+    }
+    return dyn;
+}
+
 template <typename Real, typename Store, int QF, int QT>
 cudaError_t launch_batch(const StepArgs<Real, Store> *cases, const int4 *ctas, int n_ctas, const int *active, int seg,
                          cudaStream_t s)
 {
     constexpr int TX = march_width<Real>();
-    batch_kernel<Real, Store, QF, QT, TX><<<n_ctas, TX, 0, s>>>(cases, ctas, active, seg);
+    const int dyn = prepare_kernels<Real, Store, QF, QT>();
+    batch_kernel<Real, Store, QF, QT, TX><<<n_ctas, TX + 32, dyn, s>>>(cases, ctas, active, seg);
     return cudaGetLastError();
 }
 
@@ -353,10 +596,11 @@ template <typename Real, typename Store, int QF, int QT>
 int resident_ctas()
 {
     constexpr int TX = march_width<Real>();
+    const int dyn = prepare_kernels<Real, Store, QF, QT>();
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<Real, Store, QF, QT, TX>, TX, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<Real, Store, QF, QT, TX>, TX + 32, dyn);
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
@@ -386,20 +630,20 @@ static int choose_segment(int strips, int ny, int slots)
 template <typename Real, typename Store, int QF, int QT>
 cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_rows)
 {
-    // FP64 needs ~240 registers per thread: 128-thread strips; otherwise 256
     constexpr int TX = march_width<Real>();
+    const int dyn = prepare_kernels<Real, Store, QF, QT>();
     static int slots = 0;   // resident CTAs on the device (per template instance)
     if (slots == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<Real, Store, QF, QT, TX>, TX, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<Real, Store, QF, QT, TX>, TX + 32, dyn);
         slots = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int strips = (A.nx + TX - 1) / TX;
     const int seg = seg_rows > 0 ? (seg_rows < A.ny ? seg_rows : A.ny) : choose_segment(strips, A.ny, slots);
     dim3 grid(strips, (A.ny + seg - 1) / seg);
-    march_kernel<Real, Store, QF, QT, TX><<<grid, TX, 0, s>>>(A, seg);
+    march_kernel<Real, Store, QF, QT, TX><<<grid, TX + 32, dyn, s>>>(A, seg);
     return cudaGetLastError();
 }
 
