@@ -152,8 +152,8 @@ int lbm_set_segment(lbm_handle *h, int32_t rows);
 int lbm_test_stall_copies(lbm_handle *h, int32_t on);
 
 /* Autotuner: times `reps` launches of the step kernel for each candidate segment length
- * (automatic, 8 .. 256 rows below ny) and keeps the fastest; *rows (may be NULL) receives
- * it.  The kernel is re-launched from the same input buffer, so the state and the step
+ * (the automatic choice, then 8 .. 256 rows below ny) and keeps the fastest; *rows (may be
+ * NULL) receives its row count.  The kernel is re-launched from the same input buffer, so the state and the step
  * count are unchanged.  Synchronises. */
 int lbm_autotune(lbm_handle *h, int32_t reps, int32_t *rows);
 

@@ -476,6 +476,14 @@ int lbm_run_to_steady(lbm_handle *h, double tol, int64_t max_steps, int64_t *ste
 
 }  // extern "C"
 
+template <typename R, typename S, int QF, int QT> struct AutoSegFn {
+    static cudaError_t run(const lbm_handle *h, int *rows)
+    {
+        *rows = auto_segment<R, S, QF, QT>(h->nx, h->ny);
+        return cudaGetLastError();
+    }
+};
+
 template <typename R, typename S, int QF, int QT> struct GetFn {
     static cudaError_t run(const lbm_handle *h, double *stage, int lattice, int Q, int toStore)
     {
@@ -662,12 +670,15 @@ int lbm_test_stall_copies(lbm_handle *h, int32_t on)
 int lbm_autotune(lbm_handle *h, int32_t reps, int32_t *rows)
 {
     if (!h || reps < 1) return LBM_EINVAL;
-    // candidates: automatic, then fixed segment lengths up to the channel height
+    // candidates: the automatic choice (whole waves), then fixed segment lengths up to the
+    // channel height
     int cand[16], nc = 0;
-    cand[nc++] = 0;
+    int autoseg = 0;
+    CK(dispatch<AutoSegFn>(h, &autoseg));
+    cand[nc++] = autoseg;
     const int fixed[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256};
     for (int f : fixed)
-        if (f < h->ny && nc < 16) cand[nc++] = f;
+        if (f < h->ny && f != autoseg && nc < 16) cand[nc++] = f;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

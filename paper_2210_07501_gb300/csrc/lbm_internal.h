@@ -20,6 +20,8 @@ cudaError_t launch_batch(const StepArgs<Real, Store> *cases, const int4 *ctas, i
 // Columns per strip of the step kernel, and CTAs of the batch kernel resident on the device.
 template <typename Real, typename Store, int QF, int QT> int step_strip_width();
 template <typename Real, typename Store, int QF, int QT> int resident_ctas();
+// Rows per segment the step kernel picks when none is set (whole waves of resident CTAs).
+template <typename Real, typename Store, int QF, int QT> int auto_segment(int nx, int ny);
 
 // Initialisation: macro [5][ny][nx] (phi, u, v, T, dp) holds the fields; entries whose
 // bit in `defaults` (1 phi, 2 u, 4 v, 8 T, 16 dp) is set are filled with the defaults

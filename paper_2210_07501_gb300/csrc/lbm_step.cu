@@ -627,12 +627,13 @@ static int choose_segment(int strips, int ny, int slots)
     return best;
 }
 
+// resident CTAs of the step kernel on the device (per template instance)
 template <typename Real, typename Store, int QF, int QT>
-cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_rows)
+static int march_slots()
 {
     constexpr int TX = march_width<Real>();
     const int dyn = prepare_kernels<Real, Store, QF, QT>();
-    static int slots = 0;   // resident CTAs on the device (per template instance)
+    static int slots = 0;
     if (slots == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
@@ -640,9 +641,23 @@ cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_kernel<Real, Store, QF, QT, TX>, TX + 32, dyn);
         slots = sms * (per_sm > 0 ? per_sm : 1);
     }
-    const int strips = (A.nx + TX - 1) / TX;
-    const int seg = seg_rows > 0 ? (seg_rows < A.ny ? seg_rows : A.ny) : choose_segment(strips, A.ny, slots);
-    dim3 grid(strips, (A.ny + seg - 1) / seg);
+    return slots;
+}
+
+template <typename Real, typename Store, int QF, int QT>
+int auto_segment(int nx, int ny)
+{
+    constexpr int TX = march_width<Real>();
+    return choose_segment((nx + TX - 1) / TX, ny, march_slots<Real, Store, QF, QT>());
+}
+
+template <typename Real, typename Store, int QF, int QT>
+cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_rows)
+{
+    constexpr int TX = march_width<Real>();
+    const int dyn = prepare_kernels<Real, Store, QF, QT>();
+    const int seg = seg_rows > 0 ? (seg_rows < A.ny ? seg_rows : A.ny) : auto_segment<Real, Store, QF, QT>(A.nx, A.ny);
+    dim3 grid((A.nx + TX - 1) / TX, (A.ny + seg - 1) / seg);
     march_kernel<Real, Store, QF, QT, TX><<<grid, TX + 32, dyn, s>>>(A, seg);
     return cudaGetLastError();
 }
@@ -652,6 +667,7 @@ cudaError_t launch_step(const StepArgs<Real, Store> &A, cudaStream_t s, int seg_
     template cudaError_t launch_batch<R, S, QF, QT>(const StepArgs<R, S> *, const int4 *, int, const int *, \
                                                     int, cudaStream_t);                                   \
     template int step_strip_width<R, S, QF, QT>();                                                         \
+    template int auto_segment<R, S, QF, QT>(int, int);                                                     \
     template int resident_ctas<R, S, QF, QT>();
 LBM_INST(double, double, 5, 5)
 LBM_INST(double, double, 5, 9)
