@@ -33,7 +33,8 @@ import lbm_workloads as WL  # noqa: E402
 
 METRIC = "MLUPS (coupled 3-lattice step) & HBM GB/s vs peak; sweep time-to-steady, warm vs cold"
 WORKLOAD = "srf-channel-8192x2048"
-PRECISION = "fp32"
+PRECISION = "fp32"   # storage of the benchmark line (--precision changes it)
+KERNEL_TYPES = {"fp32": "float,float", "fp16": "float,__half", "fp64": "double,double"}
 CHECK_INTERVAL = 100
 
 
@@ -259,7 +260,7 @@ def bench_gpu(args):
     N = nx * ny
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        g = pkg.Lbm(w["domain"], w["params"], precision=PRECISION, stream=stream)
+        g = pkg.Lbm(w["domain"], w["params"], precision=args.precision, stream=stream)
         g.lbm_set_check_interval(CHECK_INTERVAL)
         bpn = g.lbm_bytes_per_node()
         if args.segment:
@@ -297,16 +298,17 @@ def bench_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "b": w["domain"]["b"], "W": w["domain"]["W"],
-                   "lattices": "D2Q9 flow + D2Q5 phase field + D2Q5 energy", "storage": PRECISION,
+                   "lattices": "D2Q9 flow + D2Q5 phase field + D2Q5 energy", "storage": args.precision,
                    "check_interval": CHECK_INTERVAL, "l2": "working set 2.7 GB > L2 (no flush needed)",
                    "segment_rows": seg_rows,
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(),
+                     "frac": achieved / peak, "traffic": ncu_traffic() if args.precision == PRECISION else None,
                      "bytes_per_node": bpn, "peak_source": peak_kind,
-                     "kernel": "lbm::march_kernel<float,float,5,5,128> (+ reductions every 100 steps in the region)"},
+                     "kernel": f"lbm::march_kernel<{KERNEL_TYPES[args.precision]},5,5,128> "
+                               "(+ reductions every 100 steps in the region)"},
         "e2e": e2e,
         "gpu_launches": gpu_launches,
         "clocks": clocks,
@@ -394,6 +396,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--ny", type=int, default=0, help="rows of a shorter channel (profiling); 0 = full")
     ap.add_argument("--segment", type=int, default=0, help="rows per CTA segment; 0 = autotune")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "fp64"], default=PRECISION,
+                    help="storage precision (fp16: FP32 arithmetic; fp64: FP64 throughout)")
     ap.add_argument("--sweep", type=int, default=0, help="run the batched-sweep comparison on N channels")
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)

@@ -61,8 +61,20 @@ PAPER_SRF_200x100 = _cfg("paper-srf-channel-200x100",
                          sigma0=1e-2, sigma1=0.0, sigma2=1e-3, tau_phi=0.56,
                          tau_flow=1.17, tau_T=2.73)
 
+# The paper's droplet case (Sec. 5.1): a 2-D drop of radius R = 20 at the centre of an
+# 8R x 16R box, periodic in x, no-slip walls at T = 0 (bottom) and T = 32 (top), i.e. a
+# uniform far-field gradient of 0.1; rho = c_p = 1, mu = k = 0.2 in both fluids, T_ref = 16,
+# sigma0 = 2.5e-3, sigma_T = -1e-4.  nu = alpha = 0.2 give tau = 3 (0.2) + 1/2 = 1.1.  W and
+# M_phi are not printed for this case: W = 5 and M_phi = 0.02 (tau_phi = 0.56) as in Sec. 5.2.
+# The domain's b only feeds the default layer initialisation, which this case replaces.
+PAPER_DROP_160x320 = _cfg("paper-drop-migration-160x320",
+                          dict(nx=160, ny=320, b=160.0, W=5.0, heat_periods=1, q_phi=9, q_T=9),
+                          sigma0=2.5e-3, sigma1=-1e-4, sigma2=0.0, T_ref=16.0, T_hot=0.0, T_cold=32.0,
+                          dT=0.0, tau_flow=1.1, tau_T=1.1, tau_phi=0.56)
+DROP_RADIUS = 20.0
+
 WORKLOADS = {w["name"]: w for w in (SRF_128x32, SRF_1024x256, SRF_8192x2048,
-                                     PAPER_NF_200x100, PAPER_SRF_200x100)}
+                                     PAPER_NF_200x100, PAPER_SRF_200x100, PAPER_DROP_160x320)}
 
 
 def workload(name: str, **domain_over) -> dict:
@@ -106,6 +118,23 @@ def random_fields(nx: int, ny: int, seed: int, u_amp=1e-3, T_amp=0.2, dp_amp=1e-
 
     return {"phi_pert": smooth(phi_amp), "u": smooth(u_amp), "v": smooth(u_amp),
             "T_pert": smooth(T_amp), "dp": smooth(dp_amp)}
+
+
+def drop_fields(nx: int, ny: int, R: float, W: float, T_bottom: float, T_top: float,
+                xc=None, yc=None) -> dict:
+    """Initial fields of a drop case: phi = 1 inside a circle of radius R centred at
+    (xc, yc) (default: the box centre) with a tanh edge of width W, the conduction profile
+    between the wall temperatures (walls half a node outside the first and last rows), the
+    fluid at rest and dp = 0.  Arrays [ny][nx]; node (i, j) sits at (i, j + 1/2)."""
+    xc = nx / 2.0 if xc is None else xc
+    yc = ny / 2.0 if yc is None else yc
+    x = np.arange(nx)[None, :] + 0.0
+    y = np.arange(ny)[:, None] + 0.5
+    r = np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    phi = 0.5 + 0.5 * np.tanh(2.0 * (R - r) / W)
+    T = np.broadcast_to(T_bottom + (T_top - T_bottom) * y / ny, (ny, nx)).copy()
+    z = np.zeros((ny, nx))
+    return {"phi": phi, "u": z, "v": z.copy(), "T": T, "dp": z.copy()}
 
 
 def sweep_cases(n_cases: int = 96, seed: int = 0) -> list:

@@ -604,23 +604,22 @@ int resident_ctas()
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-// Segment length: the grid (strips x segments) is made as close as possible to a whole
-// number of waves of resident CTAs, preferring long segments (each segment re-derives 4
-// rows of phi and 2 of sigma to start its window).
+// Segment length: the one that minimises the estimated step time, waves of resident CTAs
+// times (rows per segment + the ~6 start-up rows each segment re-derives), preferring longer
+// segments on ties.  Small grids get short segments (more CTAs in one wave); large grids
+// whole waves.  Segments are at least 8 rows.
 static int choose_segment(int strips, int ny, int slots)
 {
-    int best = ny, best_key = -1;
+    int best = ny;
+    long long best_cost = -1;
     for (int nseg = 1; nseg <= (ny + 7) / 8; ++nseg) {
         const int seg = (ny + nseg - 1) / nseg;
         const int used = (ny + seg - 1) / seg;          // segments actually launched
         const long long ctas = (long long)strips * used;
         const long long waves = (ctas + slots - 1) / slots;
-        // efficiency in per-mille, then longer segments first
-        const int eff = int(1000 * ctas / (waves * slots));
-        const int warm = int(1000 * 6 / (seg + 6));     // start-up rows per segment
-        const int key = eff - warm;
-        if (key > best_key) {
-            best_key = key;
+        const long long cost = waves * (seg + 6);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
             best = seg;
         }
     }
