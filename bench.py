@@ -369,6 +369,27 @@ def bench_sweep(args):
     return 0
 
 
+def bench_trends(args):
+    """The parametric study of Sec. 6 as one batched FP64 sweep: U_max on the interface
+    against k~ and mu~ for a/b = 1/3, 1, 3 and against M2, beside the closed form of Sec. 3."""
+    import paper_2210_07501_gb300 as pkg
+    from paper_2210_07501_gb300 import trends as T
+    pkg.build()
+    pkg.load()
+    cl = (T.cases("cond_ratio", (0.25, 0.5, 1.0, 2.0, 4.0)) + T.cases("visc_ratio", (0.25, 0.5, 2.0, 4.0)) +
+          T.cases("M2", (2.5e-2, 1e-1), ab_values=(1.0,)))
+    res, seconds = T.run(cl, tol=args.sweep_tol if args.sweep_tol < 1e-5 else 1e-6, max_steps=args.sweep_max)
+    sites = sum(c["domain"]["nx"] * c["domain"]["ny"] for c in cl)
+    lu = sum(c["domain"]["nx"] * c["domain"]["ny"] * r["steps"] for c, r in zip(cl, res))
+    line = {"trends": {"cases": len(cl), "precision": "fp64", "seconds": seconds, "sites_total": sites,
+                       "batched_mlups": lu / seconds / 1e6,
+                       "rows": [{"name": r["name"], "steps": r["steps"], "converged": r["converged"],
+                                 "U_lb": r["U_lb"], "U_closed_form": r["U_closed_form"],
+                                 "ratio": r["U_lb"] / r["U_closed_form"]} for r in res]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def bench_warmstart(args):
     """Learned warm start: surrogate trained on solver-generated steady channels (256 x 64),
     then warm vs cold starts on held-out seeds."""
@@ -399,6 +420,7 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp16", "fp64"], default=PRECISION,
                     help="storage precision (fp16: FP32 arithmetic; fp64: FP64 throughout)")
     ap.add_argument("--sweep", type=int, default=0, help="run the batched-sweep comparison on N channels")
+    ap.add_argument("--trends", action="store_true", help="run the Sec. 6 parametric study (U_max trends)")
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)
     ap.add_argument("--warmstart", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
@@ -413,6 +435,8 @@ def main(argv=None):
         return bench_sweep(args)
     if args.warmstart:
         return bench_warmstart(args)
+    if args.trends:
+        return bench_trends(args)
     return bench_gpu(args)
 
 
