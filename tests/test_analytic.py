@@ -129,7 +129,8 @@ def test_printed_droplet_velocity():
     assert abs(u - g["U_ygb"]) <= g["rel_tol"] * g["U_ygb"]
 
 
-@pytest.mark.parametrize("key", ["nf_channel_Ca", "srf_channel_Ca"])
+@pytest.mark.parametrize("key", ["nf_channel_Ca", "srf_channel_Ca",
+                                 "srf_deformation_Ca_M2_3", "srf_deformation_Ca_M2_5", "srf_deformation_Ca_M2_10", "srf_deformation_Ca_M2_20"])
 def test_printed_capillary_numbers(key):
     """Ca = U_s mu_b / sigma0 with U_s of App. C reproduces the printed Ca (2 digits)."""
     g = GOLD[key]
@@ -138,7 +139,8 @@ def test_printed_capillary_numbers(key):
     assert abs(Ca - g["Ca"]) <= g["rel_tol"] * g["Ca"] + 5e-5
 
 
-@pytest.mark.parametrize("key", ["nf_channel_Ca", "srf_channel_Ca", "srf_mixed_small_M1", "srf_mixed_large_M1"])
+@pytest.mark.parametrize("key", ["nf_channel_Ca", "srf_channel_Ca", "srf_mixed_small_M1", "srf_mixed_large_M1",
+                                 "srf_deformation_Ca_M2_3", "srf_deformation_Ca_M2_5", "srf_deformation_Ca_M2_10", "srf_deformation_Ca_M2_20"])
 def test_printed_vortex_counts_and_direction(key):
     g = GOLD[key]
     c = _chan(l=g["l"], a=g["a"], b=g["b"], sigma_T=g["M1"] * g["sigma0"], sigma_TT=g["M2"] * g["sigma0"])

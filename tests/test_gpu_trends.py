@@ -52,3 +52,27 @@ def test_u_max_trends_match_closed_form():
     # U_max is linear in M2 at M1 = 0
     u25, u50, u100 = U["trend-ab=1,M2=0.025"], U["trend-ab=1,cond_ratio=1"], U["trend-ab=1,M2=0.1"]
     assert abs(u50 / u25 - 2.0) < 0.02 and abs(u100 / u50 - 2.0) < 0.02
+
+
+@pytest.mark.timeout(600)
+def test_interface_deforms_more_at_larger_capillary_number():
+    """Sec. 6, last study: a/b = 3, M2 = 3 .. 20 (Ca = 0.34 .. 2.29 by the analytic U_s, which
+    reproduces the printed ladder): the interface deflects more as Ca grows, the layer
+    volume is kept (mean height b), and the eight cells of the SRF layers persist."""
+    from oracle import analytic as A
+    from paper_2210_07501_gb300 import trends as T
+    res, seconds = T.run_deformation()
+    print(f"deformation sweep: {seconds:.1f} s")
+    for r in res:
+        c = A.Channel(l=200, a=75, b=25, k_ratio=1, mu_ratio=1, mu_b=(1.17 - 0.5) / 3, sigma_T=0.0,
+                      sigma_TT=r["M2"] * 1e-3)
+        r["Ca"] = abs(A.U_s(c)) * c.mu_b / 1e-3
+        print(f"{r['name']:20s} Ca {r['Ca']:.3f} steps {r['steps']:6d} conv {r['converged']} "
+              f"deflection {r['deflection']:.3f} mean height {r['mean_height']:.3f} cells {r['cells']} "
+              f"u_max {r['u_max']:.3e}")
+    d = [r["deflection"] for r in res]
+    assert all(r["cells"] == 8 for r in res)
+    assert all(abs(r["mean_height"] - 25.0) < 0.5 for r in res)
+    assert d[0] < 0.05                                   # Ca = 0.011: flat, the analytic regime
+    assert all(d[i] < d[i + 1] for i in range(len(d) - 1))
+    assert d[-1] > 10 * d[1]                             # Ca 2.29 vs 0.34
