@@ -390,6 +390,50 @@ def bench_trends(args):
     return 0
 
 
+def bench_steady(args):
+    """The 1024 x 256 channel (sigma1 = 2e-5) run toward steady state in FP64 and FP32 from
+    the closed-form temperature: residual history, and the steady fields against the closed
+    form of Sec. 3 (interface velocity and temperature)."""
+    import paper_2210_07501_gb300 as pkg
+    from paper_2210_07501_gb300 import surrogate as S
+    from paper_2210_07501_gb300 import trends as T
+    pkg.build()
+    pkg.load()
+    w = WL.workload("srf-channel-1024x256", sigma1=2e-5)
+    d, p = w["domain"], w["params"]
+    T_cf, u_cf, _ = S.closed_form(d, p)
+    out = {}
+    for prec, tol in (("fp32", 1e-5), ("fp64", args.steady_tol)):
+        g = pkg.Lbm(d, p, precision=prec)
+        g.lbm_set_check_interval(100)
+        g.lbm_init_fields(T=T_cf)
+        g.lbm_autotune(3)
+        hist, done, t0 = [], 0, time.perf_counter()
+        chunk = 50000
+        ok = False
+        while done < args.sweep_max and not ok:
+            ok, n = g.lbm_run_to_steady(tol, min(chunk, args.sweep_max - done))
+            done += n
+            hist.append([done, g.lbm_diag()["residual"]])
+        secs = time.perf_counter() - t0
+        f = g.lbm_fields()
+        g.close()
+        j = int(round(d["b"]))
+        Ti = 0.5 * (f["T"][j - 1] + f["T"][j]) - p["T_ref"]
+        Ti_cf = 0.5 * (T_cf[j - 1] + T_cf[j]) - p["T_ref"]
+        out[prec] = {"tol": tol, "converged": bool(ok), "steps": done, "seconds": secs,
+                     "residual_history": hist, "U_lb": T.interface_u_max(f["u"], d["b"]),
+                     "U_closed_form": T.interface_u_max(u_cf, d["b"]),
+                     "T_interface_rel": float(np.linalg.norm(Ti - Ti_cf) / np.linalg.norm(Ti_cf)),
+                     "u": f["u"]}
+    du = float(np.linalg.norm(out["fp32"]["u"] - out["fp64"]["u"]) / np.linalg.norm(out["fp64"]["u"]))
+    for v in out.values():
+        v.pop("u")
+    print(json.dumps({"steady": {"workload": "srf-channel-1024x256 (sigma1 = 2e-5)", "runs": out,
+                                 "u_fp32_vs_fp64_rel_l2": du}}), flush=True)
+    return 0
+
+
 def bench_warmstart(args):
     """Learned warm start: surrogate trained on solver-generated steady channels (256 x 64),
     then warm vs cold starts on held-out seeds."""
@@ -421,6 +465,8 @@ def main(argv=None):
                     help="storage precision (fp16: FP32 arithmetic; fp64: FP64 throughout)")
     ap.add_argument("--sweep", type=int, default=0, help="run the batched-sweep comparison on N channels")
     ap.add_argument("--trends", action="store_true", help="run the Sec. 6 parametric study (U_max trends)")
+    ap.add_argument("--steady", action="store_true", help="1024 x 256 channel to steady state, FP32 and FP64")
+    ap.add_argument("--steady-tol", type=float, default=1e-8)
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)
     ap.add_argument("--warmstart", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
@@ -437,6 +483,8 @@ def main(argv=None):
         return bench_warmstart(args)
     if args.trends:
         return bench_trends(args)
+    if args.steady:
+        return bench_steady(args)
     return bench_gpu(args)
 
 

@@ -122,3 +122,28 @@ def run_deformation(M2_values=(0.1, 3.0, 5.0, 10.0, 20.0), precision: str = "fp3
                     "mean_height": float(np.nanmean(h)), "cells": cell_count(f["v"], c["domain"]["b"]),
                     "u_max": float(np.abs(f["u"]).max()), "height": h})
     return out, seconds
+
+
+# ---- steady state of the 1024 x 256 channel against the closed form ----
+# a = b = 128, W = 5, sigma2 = -2e-4, sigma1 in {0, 2e-5}, mu~ = k~ = 2, tau_b = 0.8.  The run
+# starts from the closed-form temperature (the slowest mode of the approach to steady state is
+# thermal) with the fluid at rest, and stops at r <= tol or max_steps.
+
+def steady_vs_closed_form(cases: list, precision: str = "fp64", tol: float = 1e-8, max_steps: int = 1500000,
+                          stream=None) -> list:
+    init = [{"T": S.closed_form(c["domain"], c["params"])[0]} for c in cases]
+    fields, steps, conv, seconds = steady_batch(cases, tol, max_steps, precision, init=init, stream=stream)
+    out = []
+    for c, f, n, ok in zip(cases, fields, steps, conv):
+        d, p = c["domain"], c["params"]
+        T_cf, u_cf, v_cf = S.closed_form(d, p)
+        b = d["b"]
+        j = int(round(b))
+        rel = lambda a, e: float(np.linalg.norm(a - e) / max(np.linalg.norm(e), 1e-300))
+        Ti = 0.5 * (f["T"][j - 1] + f["T"][j]) - p["T_ref"]
+        Ti_cf = 0.5 * (T_cf[j - 1] + T_cf[j]) - p["T_ref"]
+        out.append({"name": c["name"], "steps": int(n), "converged": bool(ok), "seconds": seconds,
+                    "U_lb": interface_u_max(f["u"], b), "U_closed_form": interface_u_max(u_cf, b),
+                    "T_interface_rel": rel(Ti, Ti_cf), "T_rel": rel(f["T"] - p["T_ref"], T_cf - p["T_ref"]),
+                    "u_rel": rel(f["u"], u_cf), "v_rel": rel(f["v"], v_cf), "fields": f})
+    return out
