@@ -318,6 +318,8 @@ def bench_gpu(args):
         line["config"]["reduced_rows_for_profiling"] = args.ny
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_sample(args.cpu_budget, 0)
+        one = run_cpu_sample(args.cpu_budget / 3.0, 1)      # the same oracle on one host thread
+        line["cpu_baseline"]["single_thread"] = {"value": one["value"], "unit": one["unit"], "sample": one["sample"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
