@@ -497,23 +497,27 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             collide_flow_(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy);
             collide_energy_<QT>(hq0, dT, ux, uy, P.T_ref, om_T);
             const int o = y * pitch + x;
+            // one unsigned 32-bit byte offset from every plane's base (measured 2 % faster than
+            // plane base + element index)
+            const uint32_t ob = uint32_t(o) * uint32_t(sizeof(Store));
+            auto at = [&](Store *base) { return reinterpret_cast<Store *>(reinterpret_cast<char *>(base) + ob); };
 #pragma unroll
             for (int a = 0; a < QF; ++a) {
                 Real v = fq0[a];
                 if constexpr (scaled_<Store>()) v *= A.sf;
-                st_(A.fo[a] + o, v);
+                st_(at(A.fo[a]), v);
             }
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
                 Real v = g[a];
                 if constexpr (scaled_<Store>()) v *= A.sg;
-                st_(A.go[a] + o, v);
+                st_(at(A.go[a]), v);
             }
 #pragma unroll
             for (int a = 0; a < QT; ++a) {
                 Real v = hq0[a];
                 if constexpr (scaled_<Store>()) v *= A.sh;
-                st_(A.ho[a] + o, v);
+                st_(at(A.ho[a]), v);
             }
             A.dp_out[o] = dp;
             if (A.macro) {
