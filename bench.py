@@ -405,7 +405,10 @@ def bench_steady(args):
     d, p = w["domain"], w["params"]
     T_cf, u_cf, _ = S.closed_form(d, p)
     out = {}
-    for prec, tol in (("fp32", 1e-5), ("fp64", args.steady_tol)):
+    runs = (("fp32", 1e-5), ("fp64", args.steady_tol))
+    if args.steady_only:
+        runs = tuple(r for r in runs if r[0] == args.steady_only)
+    for prec, tol in runs:
         g = pkg.Lbm(d, p, precision=prec)
         g.lbm_set_check_interval(100)
         g.lbm_init_fields(T=T_cf)
@@ -428,7 +431,8 @@ def bench_steady(args):
                      "U_closed_form": T.interface_u_max(u_cf, d["b"]),
                      "T_interface_rel": float(np.linalg.norm(Ti - Ti_cf) / np.linalg.norm(Ti_cf)),
                      "u": f["u"]}
-    du = float(np.linalg.norm(out["fp32"]["u"] - out["fp64"]["u"]) / np.linalg.norm(out["fp64"]["u"]))
+    du = (float(np.linalg.norm(out["fp32"]["u"] - out["fp64"]["u"]) / np.linalg.norm(out["fp64"]["u"]))
+          if len(out) == 2 else None)
     for v in out.values():
         v.pop("u")
     print(json.dumps({"steady": {"workload": "srf-channel-1024x256 (sigma1 = 2e-5)", "runs": out,
@@ -469,6 +473,7 @@ def main(argv=None):
     ap.add_argument("--trends", action="store_true", help="run the Sec. 6 parametric study (U_max trends)")
     ap.add_argument("--steady", action="store_true", help="1024 x 256 channel to steady state, FP32 and FP64")
     ap.add_argument("--steady-tol", type=float, default=1e-8)
+    ap.add_argument("--steady-only", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)
     ap.add_argument("--warmstart", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
