@@ -111,7 +111,7 @@ int lbm_fields(lbm_handle *h, double *phi, double *u, double *v, double *T, doub
  * LBM_DTYPE_F32 (e.g. torch tensors).  Asynchronous on the handle's stream. */
 int lbm_fields_device(lbm_handle *h, void *phi, void *u, void *v, void *T, void *dp, int dtype);
 
-/* Global diagnostics (spec reductions, FP64 accumulation in a fixed order):
+/* Global diagnostics (reductions with FP64 accumulation in a fixed order):
  * mass = sum of phi over the lattice at the current step; residual = ||u^n - u^{n-K}||_2 /
  * (K ||u^n||_2) over both components from the last two checks K steps apart (-1 before
  * two checks); step = steps taken.  Returns LBM_EUNSTABLE if a non-finite value was seen.
@@ -234,7 +234,8 @@ void lbm_batch_destroy(lbm_batch *b);
 /* ---- learned warm start: a small convolutional surrogate of the steady fields ----
  * Not a step of the paper's method: it predicts the steady phi, u, v, T of a channel from
  * its parameters and heating profile, and its prediction initialises the LB solver
- * (lbm_init_fields), which then converges to the LB solution and judges the error.
+ * (lbm_init_fields), which then converges to the LB solution; the surrogate's error is
+ * measured against that solution.
  * Network: six 3x3 convolutions, channels 12 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, SiLU between
  * layers, periodic in x, zero padding in y; FP32 weights, activations stored in BF16
  * (bf16_activations != 0) or FP32, FP32 accumulation.  Parameters, in order per layer:

@@ -107,39 +107,6 @@ __device__ __forceinline__ int mirror_row_(int y, int ny)
     return y < 0 ? 0 : (y >= ny ? ny - 1 : y);
 }
 
-// ---- pull streaming with the wall rules ----
-// KIND 0: phase field, specular reflection (free slip, no flux through the wall)
-// KIND 1: flow, halfway bounce-back (no slip)
-// KIND 2: energy, anti-bounce-back to the wall temperature at the link's crossing point
-template <int KIND, int Q, typename Real, typename Store>
-__device__ __forceinline__ void pull_(const Store *__restrict__ base, long long plane, int pitch, int nx, int ny,
-                                      int x, int xm, int xp, int y, Real iscale, const Real *__restrict__ twall,
-                                      Real dTcold, Real *out)
-{
-    const long long row = (long long)y * pitch;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        const int ex = ex_(a), ey = ey_(a);
-        const int xs = ex > 0 ? xm : (ex < 0 ? xp : x);
-        const bool wall = (ey > 0 && y == 0) || (ey < 0 && y == ny - 1);
-        Real v;
-        if (!wall) {
-            const long long rs = ey > 0 ? row - pitch : (ey < 0 ? row + pitch : row);
-            v = ld_<Real, Store>(base + a * plane + rs + xs);
-        } else if (KIND == 0) {
-            v = ld_<Real, Store>(base + mir_(a) * plane + row + xs);
-        } else {
-            v = ld_<Real, Store>(base + opp_(a) * plane + row + x);
-        }
-        if constexpr (scaled_<Store>()) v *= iscale;
-        if (KIND == 2 && wall) {
-            // link from (x, y) towards the wall crosses it at x - e_x / 2
-            const Real tw = ey > 0 ? twall[(1 - ex) * nx + x] : dTcold;
-            v = -v + Real(2.0 * w_<Q>(a)) * tw;
-        }
-        out[a] = v;
-    }
-}
 
 // ---- isotropic finite differences on a shared-memory tile:
 // d_i psi = (1/c^2) sum_a w_a e_ai psi(x + e_a) with the D2Q9 weights ----
@@ -150,16 +117,6 @@ __device__ __forceinline__ void iso_grad_(const Real (*s)[LD], int y, int x, Rea
     const Real ne = s[y + 1][x + 1], nw = s[y + 1][x - 1], se = s[y - 1][x + 1], sw = s[y - 1][x - 1];
     gx = c1 * (s[y][x + 1] - s[y][x - 1]) + c2 * ((ne - nw) + (se - sw));
     gy = c1 * (s[y + 1][x] - s[y - 1][x]) + c2 * ((ne - se) + (nw - sw));
-}
-template <typename Real, int LD>
-__device__ __forceinline__ Real iso_div_(const Real (*sx)[LD], const Real (*sy)[LD], int y, int x)
-{
-    const Real c1 = Real(1.0 / 3.0), c2 = Real(1.0 / 12.0);
-    const Real dx = c1 * (sx[y][x + 1] - sx[y][x - 1]) +
-                    c2 * ((sx[y + 1][x + 1] - sx[y + 1][x - 1]) + (sx[y - 1][x + 1] - sx[y - 1][x - 1]));
-    const Real dy = c1 * (sy[y + 1][x] - sy[y - 1][x]) +
-                    c2 * ((sy[y + 1][x + 1] - sy[y - 1][x + 1]) + (sy[y + 1][x - 1] - sy[y - 1][x - 1]));
-    return dx + dy;
 }
 
 template <typename Real>

@@ -56,6 +56,9 @@ __device__ __forceinline__ Real rcp_(Real x)
 // Loads of one row for the pull: populations of one lattice (plane base pointers `pl`,
 // wall rule KIND) at row y and column x, with the wall rules of Sec. 5.1.  Offsets are
 // 32-bit element indices; the row part is CTA-uniform.
+//   KIND 0: phase field, specular reflection (free slip, no flux through the wall)
+//   KIND 1: flow, halfway bounce-back (no slip)
+//   KIND 2: energy, anti-bounce-back to the wall temperature where the link crosses the wall
 template <int KIND, int Q, typename Real, typename Store>
 __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int ny, int nx, int y, int x, int xm,
                                           int xp, Real iscale, const Real *__restrict__ twall, Real dTcold, Real *out)

@@ -6,7 +6,7 @@
    profile -> steady phi, T - T_ref, u/U, v/U (see `surrogate`), with Adam on the mean
    squared error; data stays on the GPU.
 3. Evaluation on held-out channels: the LB solver started from the surrogate's temperature
-   (warm) against the solver started from rest (cold, the plain method and the judge):
+   (warm) against the solver started from rest (cold, the plain method and the reference):
    steps and wall time to the tolerance, the surrogate's own error against the converged LB
    fields, and the difference between the warm- and cold-started converged fields.
    The warm start takes T only: the velocity follows T within a viscous time, and starting
@@ -149,7 +149,7 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
                           "steps_mean_on_cold_converged": float(sv[bv].mean()) if bv.size else None,
                           "cold_steps_mean_same_cases": float(s_cold[bv].mean()) if bv.size else None,
                           "fewer_steps_cases": int(np.sum(sv < s_cold))}
-    # the surrogate's own error against the converged cold-start LB fields (the judge)
+    # the surrogate's own error against the converged cold-start LB fields (the reference)
     pred_fields = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True) for c, p in zip(test_cases, P)]
     sur_err = {k: float(np.mean([rel_l2(i[k], f[k]) if k != "T" else
                                  rel_l2(i[k] - c["params"]["T_ref"], f[k] - c["params"]["T_ref"])

@@ -1,7 +1,7 @@
 """The learned warm start gains over the plain cold start: a surrogate trained (with the
 library's own kernels) on steady channels produced by the batched solver, then used to
 initialise held-out channels, which reach the tolerance in fewer steps and converge to the
-same LB solution as the cold start (the judge of the surrogate's error)."""
+same LB solution as the cold start (the reference for the surrogate's error)."""
 import numpy as np
 import pytest
 
@@ -30,7 +30,7 @@ def test_warm_start_gains_over_cold_start():
     assert r["warm_steps_mean_converged"] < r["cold_steps_mean_converged"]
     assert sum(r["warm_steps"]) < sum(r["cold_steps"])
     assert r["warm_fewer_steps_cases"] >= 5
-    # the surrogate's temperature is close to the converged LB one (the judge)
+    # the surrogate's temperature is close to the converged LB one (the reference)
     assert r["surrogate_rel_l2_vs_lb"]["phi"] < 0.1 and r["surrogate_rel_l2_vs_lb"]["T"] < 0.05
     # warm- and cold-started runs converge to the same LB solution
     assert r["warm_vs_cold_final_rel_l2"]["phi"] < 1e-3
