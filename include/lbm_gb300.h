@@ -111,14 +111,16 @@ int lbm_fields(lbm_handle *h, double *phi, double *u, double *v, double *T, doub
  * LBM_DTYPE_F32 (e.g. torch tensors).  Asynchronous on the handle's stream. */
 int lbm_fields_device(lbm_handle *h, void *phi, void *u, void *v, void *T, void *dp, int dtype);
 
-/* Global diagnostics (reductions with FP64 accumulation in a fixed order):
+/* Global diagnostics (reductions with FP64 accumulation in a fixed order; the paper defines
+ * no steady-state criterion, this residual is the library's own):
  * mass = sum of phi over the lattice at the current step; residual = ||u^n - u^{n-K}||_2 /
  * (K ||u^n||_2) over both components from the last two checks K steps apart (-1 before
  * two checks); step = steps taken.  Returns LBM_EUNSTABLE if a non-finite value was seen.
  * Synchronises. */
 int lbm_diag(lbm_handle *h, double *mass, double *residual, int64_t *step);
 
-/* Steps every check_interval (K >= 1) steps between residual checks; default 100. */
+/* Steps every check_interval (K >= 1) steps between residual checks; default 100 (no
+ * counterpart in the paper). */
 int lbm_set_check_interval(lbm_handle *h, int32_t K);
 
 /* Step until residual <= tol or max_steps are taken; *steps_taken (may be NULL) receives
@@ -130,15 +132,15 @@ int lbm_run_to_steady(lbm_handle *h, double tol, int64_t max_steps, int64_t *ste
 int lbm_get_state(lbm_handle *h, double *f, double *g, double *hT, double *dp);
 int lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *hT, const double *dp);
 
-/* Checkpoint: the raw device state, step counter, domain, parameters and a CRC32 of the
- * payload.  lbm_load requires a file written for the same domain and precision and
+/* Checkpoint (no counterpart in the paper): the raw device state, step counter, domain,
+ * parameters and a CRC32 of the payload.  lbm_load requires a file written for the same domain and precision and
  * restores the state bit for bit.  LBM_EIO on a missing, truncated or corrupt file. */
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
 
-/* Launch shape of the step kernel: each CTA walks `rows` consecutive rows of a strip
- * (0 = automatic: chosen from the device's occupancy so the grid is a whole number of
- * waves).  Affects speed only, never the results. */
+/* Launch shape of the step kernel (no counterpart in the paper): each CTA walks `rows`
+ * consecutive rows of a strip (0 = automatic: the length that minimises the waves of
+ * resident CTAs times the rows each walks).  Affects speed only, never the results. */
 int lbm_set_segment(lbm_handle *h, int32_t rows);
 
 /* Test hook for the fault path (not part of the method).  The step kernel stages its
@@ -151,17 +153,19 @@ int lbm_set_segment(lbm_handle *h, int32_t rows);
  * normal stepping.  No GPU fault or trap is involved. */
 int lbm_test_stall_copies(lbm_handle *h, int32_t on);
 
-/* Autotuner: times `reps` launches of the step kernel for each candidate segment length
- * (the automatic choice, then 8 .. 256 rows below ny) and keeps the fastest; *rows (may be
- * NULL) receives its row count.  The kernel is re-launched from the same input buffer, so the state and the step
- * count are unchanged.  Synchronises. */
+/* Autotuner (no counterpart in the paper): times `reps` launches of the step kernel for
+ * each candidate segment length (the automatic choice, then 8 .. 256 rows below ny) and
+ * keeps the fastest; *rows (may be NULL) receives its row count.  The kernel is re-launched
+ * from the same input buffer, so the state and the step count are unchanged.
+ * Synchronises. */
 int lbm_autotune(lbm_handle *h, int32_t reps, int32_t *rows);
 
 /* Bytes the step kernel moves per lattice node and step (populations read and written
- * once plus the stored pressure), for roofline accounting. */
+ * once plus the stored pressure), for roofline accounting (no counterpart in the paper). */
 int lbm_bytes_per_node(const lbm_handle *h, int64_t *bytes);
 
-/* Number of step-kernel launches queued since creation (diagnostics). */
+/* Number of step-kernel launches queued since creation (diagnostics; no counterpart in the
+ * paper). */
 int lbm_launch_count(const lbm_handle *h, int64_t *launches);
 
 /* Largest node count lbm_reduce_fields_noalloc accepts. */
