@@ -373,7 +373,8 @@ def bench_sweep(args):
 
 def bench_trends(args):
     """The parametric study of Sec. 6 as one batched FP64 sweep: U_max on the interface
-    against k~ and mu~ for a/b = 1/3, 1, 3 and against M2, beside the closed form of Sec. 3."""
+    against k~ and mu~ for a/b = 1/3, 1, 3 and against M2 (the comparison with the
+    closed form of Sec. 3 is made in tests/test_gpu_trends.py)."""
     import paper_2210_07501_gb300 as pkg
     from paper_2210_07501_gb300 import trends as T
     pkg.build()
@@ -386,57 +387,8 @@ def bench_trends(args):
     line = {"trends": {"cases": len(cl), "precision": "fp64", "seconds": seconds, "sites_total": sites,
                        "batched_mlups": lu / seconds / 1e6,
                        "rows": [{"name": r["name"], "steps": r["steps"], "converged": r["converged"],
-                                 "U_lb": r["U_lb"], "U_closed_form": r["U_closed_form"],
-                                 "ratio": r["U_lb"] / r["U_closed_form"]} for r in res]}}
+                                 "U_lb": r["U_lb"]} for r in res]}}
     print(json.dumps(line), flush=True)
-    return 0
-
-
-def bench_steady(args):
-    """The 1024 x 256 channel (sigma1 = 2e-5) run toward steady state in FP64 and FP32 from
-    the closed-form temperature: residual history, and the steady fields against the closed
-    form of Sec. 3 (interface velocity and temperature)."""
-    import paper_2210_07501_gb300 as pkg
-    from paper_2210_07501_gb300 import surrogate as S
-    from paper_2210_07501_gb300 import trends as T
-    pkg.build()
-    pkg.load()
-    w = WL.workload("srf-channel-1024x256", sigma1=2e-5)
-    d, p = w["domain"], w["params"]
-    T_cf, u_cf, _ = S.closed_form(d, p)
-    out = {}
-    runs = (("fp32", 1e-5), ("fp64", args.steady_tol))
-    if args.steady_only:
-        runs = tuple(r for r in runs if r[0] == args.steady_only)
-    for prec, tol in runs:
-        g = pkg.Lbm(d, p, precision=prec)
-        g.lbm_set_check_interval(100)
-        g.lbm_init_fields(T=T_cf)
-        g.lbm_autotune(3)
-        hist, done, t0 = [], 0, time.perf_counter()
-        chunk = 50000
-        ok = False
-        while done < args.sweep_max and not ok:
-            ok, n = g.lbm_run_to_steady(tol, min(chunk, args.sweep_max - done))
-            done += n
-            hist.append([done, g.lbm_diag()["residual"]])
-        secs = time.perf_counter() - t0
-        f = g.lbm_fields()
-        g.close()
-        j = int(round(d["b"]))
-        Ti = 0.5 * (f["T"][j - 1] + f["T"][j]) - p["T_ref"]
-        Ti_cf = 0.5 * (T_cf[j - 1] + T_cf[j]) - p["T_ref"]
-        out[prec] = {"tol": tol, "converged": bool(ok), "steps": done, "seconds": secs,
-                     "residual_history": hist, "U_lb": T.interface_u_max(f["u"], d["b"]),
-                     "U_closed_form": T.interface_u_max(u_cf, d["b"]),
-                     "T_interface_rel": float(np.linalg.norm(Ti - Ti_cf) / np.linalg.norm(Ti_cf)),
-                     "u": f["u"]}
-    du = (float(np.linalg.norm(out["fp32"]["u"] - out["fp64"]["u"]) / np.linalg.norm(out["fp64"]["u"]))
-          if len(out) == 2 else None)
-    for v in out.values():
-        v.pop("u")
-    print(json.dumps({"steady": {"workload": "srf-channel-1024x256 (sigma1 = 2e-5)", "runs": out,
-                                 "u_fp32_vs_fp64_rel_l2": du}}), flush=True)
     return 0
 
 
@@ -450,8 +402,9 @@ def bench_warmstart(args):
     n_train, n_test = args.warmstart
     train = WL.surrogate_cases(n_train, seed=1000)
     test = WL.surrogate_cases(n_test, seed=2000)
-    r = warmstart.experiment(train, test, tol=args.sweep_tol, max_steps=args.sweep_max, iters=args.train_iters,
-                             batch=16, lr=1e-3, seed=0, plain_cases=n_test)
+    r = warmstart.experiment(train, test, tol=args.warm_tol, max_steps=args.warm_max, K=args.warm_k,
+                             train_tol=args.train_tol, train_max_steps=args.train_max, iters=args.train_iters,
+                             batch=16, lr=1e-3, seed=0, plain_cases=args.warm_plain)
     print(json.dumps({"warmstart": r}), flush=True)
     return 0
 
@@ -471,14 +424,17 @@ def main(argv=None):
                     help="storage precision (fp16: FP32 arithmetic; fp64: FP64 throughout)")
     ap.add_argument("--sweep", type=int, default=0, help="run the batched-sweep comparison on N channels")
     ap.add_argument("--trends", action="store_true", help="run the Sec. 6 parametric study (U_max trends)")
-    ap.add_argument("--steady", action="store_true", help="1024 x 256 channel to steady state, FP32 and FP64")
-    ap.add_argument("--steady-tol", type=float, default=1e-8)
-    ap.add_argument("--steady-only", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)
     ap.add_argument("--warmstart", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
                     help="learned warm start: train on TRAIN channels, compare on TEST channels")
     ap.add_argument("--train-iters", type=int, default=3000)
+    ap.add_argument("--warm-tol", type=float, default=1e-8, help="warm start: residual of the held-out runs")
+    ap.add_argument("--warm-k", type=int, default=1000, help="warm start: steps between residual checks")
+    ap.add_argument("--warm-max", type=int, default=3000000)
+    ap.add_argument("--warm-plain", type=int, default=0, help="warm start: held-out cases also run one by one")
+    ap.add_argument("--train-tol", type=float, default=1e-6, help="warm start: residual of the training runs")
+    ap.add_argument("--train-max", type=int, default=400000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -490,8 +446,6 @@ def main(argv=None):
         return bench_warmstart(args)
     if args.trends:
         return bench_trends(args)
-    if args.steady:
-        return bench_steady(args)
     return bench_gpu(args)
 
 

@@ -20,9 +20,11 @@
  * Conventions shared by every entry point:
  *   - Field arrays are row-major [ny][nx] doubles; row j = 0 is next to the heated wall,
  *     column i = 0 is under the heating peak.
- *   - Populations exchanged with the caller are [Q][ny][nx] doubles in the variables the
- *     solver carries: f (phase field), g - w_a p0 (flow, p0 = rho_bottom / 3) and
- *     h - w_a T_ref (energy); "dp" is p - p0.
+ *   - Populations exchanged with the caller are [Q][ny][nx] doubles: f (phase field),
+ *     g - w_a p0 (flow, p0 = rho_bottom / 3) and h - w_a T_ref (energy); "dp" is p - p0.
+ *     Internally the phase field is stored as f - r_a(y), r the populations of the flat
+ *     tanh interface of width W at y = b at rest (an exact change of variables that keeps
+ *     round-off off the interface tilt); f is rebuilt as stored + r on output.
  *   - Every function returns LBM_OK (0) or a negative LBM_E* status and never throws.
  *     A handle is not thread-safe: use one handle per host thread.
  *   - The library owns all device memory it allocates; the caller owns every buffer it
@@ -103,12 +105,15 @@ int lbm_init_fields(lbm_handle *h, const double *phi, const double *u, const dou
  * check_interval steps the macroscopic fields are stored and reduced (mass, residual). */
 int lbm_step(lbm_handle *h, int64_t nsteps);
 
-/* Macroscopic fields of the latest step (the values its collision used): phi, u, v, T and
- * p - p0, into caller-owned host arrays [ny][nx]; any pointer may be NULL.  Synchronises. */
+/* Macroscopic fields of the latest step (the values its collision used): phi = sum_a f_a
+ * (Sec. 4.1), T = sum_a h_a (Sec. 4.3), the velocity rho c^2 u = sum_a g_a e_a + c^2 F_t / 2
+ * and the pressure p = sum_a g_a + F_p . u / 2 (Sec. 4.2), returned as p - p0; into
+ * caller-owned host arrays [ny][nx]; any pointer may be NULL.  Synchronises. */
 int lbm_fields(lbm_handle *h, double *phi, double *u, double *v, double *T, double *dp);
 
-/* As lbm_fields, into caller-owned device arrays [ny][nx] of LBM_DTYPE_F64 or
- * LBM_DTYPE_F32 (e.g. torch tensors).  Asynchronous on the handle's stream. */
+/* As lbm_fields (the same macroscopic updates of Sec. 4.1-4.3), into caller-owned device
+ * arrays [ny][nx] of LBM_DTYPE_F64 or LBM_DTYPE_F32 (e.g. torch tensors).  Asynchronous on
+ * the handle's stream. */
 int lbm_fields_device(lbm_handle *h, void *phi, void *u, void *v, void *T, void *dp, int dtype);
 
 /* Global diagnostics (reductions with FP64 accumulation in a fixed order; the paper defines
@@ -127,14 +132,19 @@ int lbm_set_check_interval(lbm_handle *h, int32_t K);
  * the count.  Returns LBM_OK, LBM_ETIMEOUT, LBM_EUNSTABLE or an error. Synchronises. */
 int lbm_run_to_steady(lbm_handle *h, double tol, int64_t max_steps, int64_t *steps_taken);
 
-/* Post-collision state in solver variables (see conventions): f [q_phi][ny][nx],
- * g [9][ny][nx], h [q_T][ny][nx], dp [ny][nx] (pressure used by the next step's force). */
+/* Post-collision state (Sec. 4.1-4.3, after the collision of the latest step) in the
+ * variables of the conventions above: f [q_phi][ny][nx], g [9][ny][nx], h [q_T][ny][nx],
+ * dp [ny][nx] (pressure used by the next step's force).  g, h and dp round-trip exactly
+ * through lbm_set_state / lbm_get_state in FP64 storage; f to within one rounding (it
+ * passes through f - r). */
 int lbm_get_state(lbm_handle *h, double *f, double *g, double *hT, double *dp);
 int lbm_set_state(lbm_handle *h, const double *f, const double *g, const double *hT, const double *dp);
 
 /* Checkpoint (no counterpart in the paper): the raw device state, step counter, domain,
- * parameters and a CRC32 of the payload.  lbm_load requires a file written for the same domain and precision and
- * restores the state bit for bit.  LBM_EIO on a missing, truncated or corrupt file. */
+ * parameters and a CRC32 of the payload.  lbm_load requires a file written for the same
+ * domain (nx, ny, q_phi, q_T, precision, b, W) and tau_phi, which fix the phase-field
+ * reference the state is stored against, and restores the state bit for bit.  LBM_EIO on
+ * a missing, truncated, corrupt or mismatched file. */
 int lbm_save(lbm_handle *h, const char *path);
 int lbm_load(lbm_handle *h, const char *path);
 
@@ -191,6 +201,9 @@ int lbm_launch_count(const lbm_handle *h, int64_t *launches);
  *
  * The first call on each device looks up the scratch array's device address (with that
  * device current) and caches it; make that first call before any stream capture begins.
+ * The cached address belongs to the device's context at that time: after
+ * cudaDeviceReset (or anything else that destroys and recreates the primary context) it
+ * is stale, so do not call this function again in such a process.
  * All calls on a device share the one scratch array: calls that overlap on the GPU (for
  * example on two streams at once) race and give wrong sums; serialise them.  Every call
  * overwrites all the scratch it reads, so leftovers of an earlier call do no harm. */
@@ -260,10 +273,12 @@ int lbm_cnn_train_step(lbm_cnn *c, const float *x, const float *target, int32_t 
 const char *lbm_cnn_strerror(void);
 void lbm_cnn_destroy(lbm_cnn *c);
 
-/* Release the handle and its device memory; NULL-safe. */
+/* Release the handle and its device memory; NULL-safe.  No counterpart in the paper
+ * (resource management of the library). */
 void lbm_destroy(lbm_handle *h);
 
-/* Static string for a status code (for LBM_ECUDA, of the last CUDA error seen). */
+/* Static string for a status code (for LBM_ECUDA, of the last CUDA error seen).  No
+ * counterpart in the paper. */
 const char *lbm_strerror(int status);
 
 #ifdef __cplusplus

@@ -1,7 +1,9 @@
 // lbm_api.cu -- host implementation of the C ABI declared in include/lbm_gb300.h.
 //
 // The handle owns two ping-pong copies of every population plane and of the stored
-// pressure, the bottom-wall temperature table, the macroscopic field buffer written by
+// pressure, the bottom-wall temperature table, the phase-field reference tables (the
+// phase-field populations are stored as deviations from a flat reference interface), the
+// macroscopic field buffer written by
 // the last step of each lbm_step call (and at every residual check), the previous
 // velocity for the residual, and the reduction scratch.  All work is queued on one CUDA
 // stream; only the entry points that return data to the host synchronise it.
@@ -30,6 +32,9 @@ struct lbm_handle {
     void *pop[2][3];        // [buffer][f, g, h]
     void *dp[2];
     void *twall;            // Real [3][nx]
+    void *rtab;             // Real [RT_N][ny + 2]: phase-field reference row tables
+    double *phi0;           // [ny] reference phi profile
+    double *fref;           // [Qf][ny] reference phase-field populations
     double *macro;          // [5][ny][nx]
     double *uprev;          // [2][ny][nx]
     double *partials;       // reduction scratch [nblk][4]
@@ -101,6 +106,9 @@ template <typename Real, typename Store> static StepArgs<Real, Store> make_args(
     A.dp_in = (const Real *)h->dp[src];
     A.dp_out = (Real *)h->dp[dst];
     A.twall = (const Real *)h->twall;
+    A.rtab = (const Real *)h->rtab;
+    A.phi0 = h->phi0;
+    A.fref = h->fref;
     A.macro = macro;
     for (int a = 0; a < 9; ++a) {
         const long long o = (long long)a * h->plane;
@@ -167,6 +175,9 @@ static void free_all(lbm_handle *h)
         if (h->dp[b]) cudaFree(h->dp[b]);
     }
     if (h->twall) cudaFree(h->twall);
+    if (h->rtab) cudaFree(h->rtab);
+    if (h->phi0) cudaFree(h->phi0);
+    if (h->fref) cudaFree(h->fref);
     if (h->macro) cudaFree(h->macro);
     if (h->uprev) cudaFree(h->uprev);
     if (h->partials) cudaFree(h->partials);
@@ -208,6 +219,118 @@ static double fp16_flow_scale(const lbm_domain *d, const lbm_params *p, double m
     if (s < 1.0) s = 1.0;
     if (s > 1073741824.0) s = 1073741824.0;
     return s;
+}
+
+// Compensated (Neumaier) summation: the sum of the terms rounded once, to within a unit in
+// the last place of the result, however much the terms cancel.
+struct KahanSum {
+    double s = 0.0, c = 0.0;
+    void add(double x)
+    {
+        const double t = s + x;
+        c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    double value() const { return s + c; }
+};
+
+// Reference state of the phase-field lattice (Sec. 4.1): the flat tanh interface of width
+// W at y = b, at rest, at its central-moment equilibrium with the normal pointing up,
+//   k_ref(y) = (p, 0, M_phi theta(p), c^2 p, c^2 p, 0, 0, 0, c^4 p),  p = tanh profile,
+//   r_a(y) = (P^-1 k_ref(y))_a  (u = 0: raw and central moments coincide).
+// The kernels carry f - r.  The change of variables is exact for the FP64 numbers r_a(y)
+// as they are, so every table is derived from those numbers: phi0(y) = sum_a r_a(y); the
+// sum of the reference populations pulled into row y under the wall rules (specular
+// reflection), R(y), enters as dR = R - phi0 = sum_a (r_a(pulled) - r_a(y)), summed with
+// compensation so that it is exact to its own last place (dR feeds sum phi every step: a
+// rounding error in it would add or remove phi each step); Ry(y) the first y moment of the
+// pulled populations and t01(y) = sum_a e_ay r_a(y) give the first-moment constant
+// c01 = (1 - omega) Ry + omega M_phi theta(phi0) - t01.  In FP32 dR is split into a high and
+// a low part, and the parts are corrected to sum to zero over the rows.
+static int build_phase_reference(lbm_handle *h)
+{
+    const int ny = h->ny, Q = h->Qf;
+    const double b = h->dom.b, W = h->dom.W, M = h->P.Mphi, om = h->P.omega_phi, c2 = 1.0 / 3.0;
+    std::vector<double> phi0(ny), r((size_t)Q * ny), tab((size_t)RT_N * (ny + 2), 0.0);
+    for (int j = 0; j < ny; ++j) {
+        const double y = j + 0.5;
+        const double p = 0.5 + 0.5 * tanh(2.0 * (y - b) / W);
+        const double t = M * 4.0 * p * (1.0 - p) / W;
+        double k[9] = {p, 0.0, t, c2 * p, c2 * p, 0.0, 0.0, 0.0, c2 * c2 * p}, f[9];
+        if (Q == 9) {
+            f[0] = k[0] - k[3] - k[4] + k[8];
+            f[1] = 0.5 * (k[1] + k[3] - k[7] - k[8]);
+            f[2] = 0.5 * (k[2] + k[4] - k[6] - k[8]);
+            f[3] = 0.5 * (-k[1] + k[3] + k[7] - k[8]);
+            f[4] = 0.5 * (-k[2] + k[4] + k[6] - k[8]);
+            f[5] = 0.25 * (k[5] + k[6] + k[7] + k[8]);
+            f[6] = 0.25 * (-k[5] + k[6] - k[7] + k[8]);
+            f[7] = 0.25 * (k[5] - k[6] - k[7] + k[8]);
+            f[8] = 0.25 * (-k[5] - k[6] + k[7] + k[8]);
+        } else {
+            f[0] = k[0] - k[3] - k[4];
+            f[1] = 0.5 * (k[1] + k[3]);
+            f[2] = 0.5 * (k[2] + k[4]);
+            f[3] = 0.5 * (k[3] - k[1]);
+            f[4] = 0.5 * (k[4] - k[2]);
+        }
+        KahanSum s;
+        for (int a = 0; a < Q; ++a) {
+            r[(size_t)a * ny + j] = f[a];
+            s.add(f[a]);
+        }
+        phi0[j] = s.value();
+    }
+    auto mirror = [ny](int y) {
+        if (y < 0) y = -1 - y;
+        if (y >= ny) y = 2 * ny - 1 - y;
+        return y < 0 ? 0 : (y >= ny ? ny - 1 : y);
+    };
+    auto T = [&](int k, int row) -> double & { return tab[(size_t)k * (ny + 2) + row + 1]; };
+    std::vector<double> dR(ny);
+    for (int j = 0; j < ny; ++j) {
+        KahanSum d, ry, t01;
+        for (int a = 0; a < Q; ++a) {
+            const int ey = ey_(a);
+            const bool wall = (ey > 0 && j == 0) || (ey < 0 && j == ny - 1);
+            const double v = wall ? r[(size_t)mir_(a) * ny + j] : r[(size_t)a * ny + (j - ey)];
+            const double own = r[(size_t)a * ny + j];
+            d.add(v);
+            d.add(-own);
+            ry.add(ey * v);
+            t01.add(ey * own);
+        }
+        dR[j] = d.value();
+        const double th0 = 4.0 * phi0[j] * (1.0 - phi0[j]) / W;
+        T(RT_PHI0, j) = phi0[j];
+        T(RT_TH0, j) = th0;
+        T(RT_C01, j) = (1.0 - om) * ry.value() + om * M * th0 - t01.value();
+    }
+    for (int j = -1; j <= ny; ++j) T(RT_GREF, j) = 0.5 * (phi0[mirror(j + 1)] - phi0[mirror(j - 1)]);
+    // dR in the kernels' precision as hi + lo, corrected so that the rows sum to zero
+    int jmin = 0;
+    KahanSum tot;
+    for (int j = 0; j < ny; ++j) {
+        const double hi = h->rsize == 8 ? dR[j] : (double)(float)dR[j];
+        const double lo = h->rsize == 8 ? 0.0 : (double)(float)(dR[j] - hi);
+        T(RT_DR, j) = hi;
+        T(RT_DRLO, j) = lo;
+        tot.add(hi);
+        tot.add(lo);
+        if (fabs(dR[j]) < fabs(dR[jmin])) jmin = j;
+    }
+    T(h->rsize == 8 ? RT_DR : RT_DRLO, jmin) -= tot.value();
+    cudaError_t e;
+    if (h->rsize == 8) {
+        e = cudaMemcpy(h->rtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> tf(tab.size());
+        for (size_t i = 0; i < tab.size(); ++i) tf[i] = (float)tab[i];
+        e = cudaMemcpy(h->rtab, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h->phi0, phi0.data(), ny * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->fref, r.data(), r.size() * sizeof(double), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e, "reference tables");
 }
 
 extern "C" {
@@ -276,6 +399,9 @@ int lbm_create(const lbm_domain *domain, const lbm_params *params, void *stream,
         ok = ok && cudaMalloc(&h->dp[b], (size_t)h->plane * h->rsize) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&h->twall, 3 * (size_t)h->nx * h->rsize) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->rtab, (size_t)RT_N * (h->ny + 2) * h->rsize) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->phi0, (size_t)h->ny * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&h->fref, (size_t)h->Qf * h->ny * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->macro, 5 * N * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->uprev, 2 * N * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->partials, (size_t)reduce_blocks() * 4 * sizeof(double)) == cudaSuccess;
@@ -316,8 +442,13 @@ int lbm_create(const lbm_domain *domain, const lbm_params *params, void *stream,
     P.Fx = p->Fx_ext;
     P.Fy = p->Fy_ext;
     P.g2min = 0.0;
-    h->sf = h->sh = 1.0;
+    // FP16: the phase-field deviations f - r stay within [-1, 1]; 2^10 keeps them in the
+    // normal range of FP16 down to ~6e-8
+    h->sf = h->prec == LBM_FP16 ? 1024.0 : 1.0;
+    h->sh = 1.0;
     h->sg = h->prec == LBM_FP16 ? fp16_flow_scale(domain, p, P.muA) : 1.0;
+    rc = build_phase_reference(h);
+    if (rc) { free_all(h); delete h; return rc; }
     // bottom-wall temperature minus T_ref at x - 1/2, x, x + 1/2 (heating peak at x = 0)
     {
         double *tw = (double *)malloc(3 * (size_t)h->nx * sizeof(double));
@@ -488,15 +619,21 @@ template <typename R, typename S, int QF, int QT> struct GetFn {
     static cudaError_t run(const lbm_handle *h, double *stage, int lattice, int Q, int toStore)
     {
         const double sc = lattice == 0 ? h->sf : (lattice == 1 ? h->sg : h->sh);
-        if (toStore) return launch_to_store<R, S>(stage, (S *)h->pop[h->cur][lattice], Q, h->nx, h->ny, h->pitch, R(sc), h->stream);
-        return launch_from_store<R, S>((const S *)h->pop[h->cur][lattice], stage, Q, h->nx, h->ny, h->pitch, R(1.0 / sc), h->stream);
+        const double *ref = lattice == 0 ? h->fref : nullptr;   // phase field: f - r stored
+        if (toStore)
+            return launch_to_store<R, S>(stage, (S *)h->pop[h->cur][lattice], Q, h->nx, h->ny, h->pitch, R(sc), ref,
+                                         h->stream);
+        return launch_from_store<R, S>((const S *)h->pop[h->cur][lattice], stage, Q, h->nx, h->ny, h->pitch,
+                                       R(1.0 / sc), ref, h->stream);
     }
 };
 template <typename R, typename S, int QF, int QT> struct DpFn {
     static cudaError_t run(const lbm_handle *h, double *stage, int toStore)
     {
-        if (toStore) return launch_to_store<R, R>(stage, (R *)h->dp[h->cur], 1, h->nx, h->ny, h->pitch, R(1), h->stream);
-        return launch_from_store<R, R>((const R *)h->dp[h->cur], stage, 1, h->nx, h->ny, h->pitch, R(1), h->stream);
+        if (toStore)
+            return launch_to_store<R, R>(stage, (R *)h->dp[h->cur], 1, h->nx, h->ny, h->pitch, R(1), nullptr, h->stream);
+        return launch_from_store<R, R>((const R *)h->dp[h->cur], stage, 1, h->nx, h->ny, h->pitch, R(1), nullptr,
+                                       h->stream);
     }
 };
 
@@ -602,7 +739,7 @@ int lbm_save(lbm_handle *h, const char *path)
     ckpt_header hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, "LBMGB300", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.step = h->step;
     hd.dom = h->dom;
     hd.prm = h->prm;
@@ -626,9 +763,11 @@ int lbm_load(lbm_handle *h, const char *path)
     if (!fp) return LBM_EIO;
     ckpt_header hd;
     const size_t bytes = state_bytes(h);
-    if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, "LBMGB300", 8) != 0 || hd.version != 1 ||
+    // the stored phase-field deviations are relative to a reference set by b, W and M_phi
+    if (fread(&hd, sizeof(hd), 1, fp) != 1 || memcmp(hd.magic, "LBMGB300", 8) != 0 || hd.version != 2 ||
         hd.payload != bytes || hd.dom.nx != h->dom.nx || hd.dom.ny != h->dom.ny || hd.dom.q_phi != h->dom.q_phi ||
-        hd.dom.q_T != h->dom.q_T || hd.dom.precision != h->dom.precision) {
+        hd.dom.q_T != h->dom.q_T || hd.dom.precision != h->dom.precision || hd.dom.b != h->dom.b ||
+        hd.dom.W != h->dom.W || hd.prm.tau_phi != h->prm.tau_phi) {
         fclose(fp);
         return LBM_EIO;
     }

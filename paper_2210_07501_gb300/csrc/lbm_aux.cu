@@ -22,7 +22,8 @@ __global__ void init_defaults_kernel(double *macro, int nx, int ny, double b, do
 }
 
 // Populations at the central-moment equilibrium of the given fields: phase field with the
-// sharpening flux M theta n in its first moments, flow and energy lattices at their
+// sharpening flux M theta n in its first moments (formed in FP64 and stored as its
+// deviation from the reference populations r_a(y)), flow and energy lattices at their
 // equilibria (no source), stored pressure = dp.
 template <typename Real, typename Store, int QF, int QT>
 __global__ void init_pop_kernel(const StepArgs<Real, Store> A)
@@ -33,38 +34,40 @@ __global__ void init_pop_kernel(const StepArgs<Real, Store> A)
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
         const int y = int(m / nx), x = int(m - (long long)y * nx);
         const double *phiF = A.macro;
-        auto phi_at = [&](int xx, int yy) -> Real {
-            return Real(phiF[(long long)mirror_row_(yy, ny) * nx + wrap_(xx, nx)]);
+        auto phi_at = [&](int xx, int yy) -> double {
+            return phiF[(long long)mirror_row_(yy, ny) * nx + wrap_(xx, nx)];
         };
-        Real s[3][3];
+        double s[3][3];
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) s[dy + 1][dx + 1] = phi_at(x + dx, y + dy);
-        Real gx, gy, nxv, nyv;
-        iso_grad_<Real, 3>(s, 1, 1, gx, gy);
-        unit_normal_(gx, gy, P.g2min, nxv, nyv);
-        const Real phi = s[1][1];
+        double gx, gy, nxv, nyv;
+        iso_grad_<double, 3>(s, 1, 1, gx, gy);
+        unit_normal_(gx, gy, double(P.g2min), nxv, nyv);
+        const double phi_d = s[1][1];
+        const Real phi = Real(phi_d);
         const Real ux = Real(A.macro[N + m]), uy = Real(A.macro[2 * N + m]);
         const Real dT = Real(A.macro[3 * N + m] - double(P.T_ref));
         const Real dp = Real(A.macro[4 * N + m]);
-        const Real theta = P.W4 * phi * (Real(1) - phi);
         const Real c2 = Real(1.0 / 3.0);
         const long long o = (long long)y * A.pitch + x;
-        // phase field
+        // phase field, in FP64, minus the reference
         {
-            Real f[QF];
-            const Real mx = P.Mphi * theta * nxv, my = P.Mphi * theta * nyv, c2p = c2 * phi;
+            double f[QF];
+            const double uxd = A.macro[N + m], uyd = A.macro[2 * N + m];
+            const double theta = double(P.W4) * phi_d * (1.0 - phi_d);
+            const double mx = double(P.Mphi) * theta * nxv, my = double(P.Mphi) * theta * nyv, c2p = phi_d / 3.0;
             if constexpr (QF == 9) {
-                const Real k[9] = {phi, mx, my, c2p, c2p, Real(0), Real(0), Real(0), phi * Real(1.0 / 9.0)};
-                central_to_pop9_(k, ux, uy, f);
+                const double k[9] = {phi_d, mx, my, c2p, c2p, 0.0, 0.0, 0.0, phi_d / 9.0};
+                central_to_pop9_(k, k, uxd, uyd, f);
             } else {
-                const Real k[5] = {phi, mx, my, c2p, c2p};
-                central_to_pop5_(k, ux, uy, f);
+                const double k[5] = {phi_d, mx, my, c2p, c2p};
+                central_to_pop5_(k, k, uxd, uyd, f);
             }
 #pragma unroll
             for (int a = 0; a < QF; ++a) {
-                Real v = f[a];
+                Real v = Real(f[a] - A.fref[a * ny + y]);
                 if constexpr (scaled_<Store>()) v *= A.sf;
                 st_(A.f_out + a * A.plane + o, v);
             }
@@ -77,7 +80,7 @@ __global__ void init_pop_kernel(const StepArgs<Real, Store> A)
             const Real k[9] = {dp, ux * d, uy * d, dp * ax - rc2 * ux2, dp * ay - rc2 * uy2, -uxy * d, ax * uy * d,
                                ay * ux * d, dp * ax * ay - rc2 * (c2 * (ux2 + uy2) + ux2 * uy2)};
             Real g[9];
-            central_to_pop9_(k, ux, uy, g);
+            central_to_pop9_(k, k, ux, uy, g);
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
                 Real v = g[a];
@@ -93,10 +96,10 @@ __global__ void init_pop_kernel(const StepArgs<Real, Store> A)
                 const Real k[9] = {dT, Tr * ux, Tr * uy, c2 * dT - Tr * ux2, c2 * dT - Tr * uy2, -Tr * ux * uy,
                                    Tr * (c2 + ux2) * uy, Tr * (c2 + uy2) * ux,
                                    Real(1.0 / 9.0) * dT - Tr * (c2 * (ux2 + uy2) + ux2 * uy2)};
-                central_to_pop9_(k, ux, uy, h);
+                central_to_pop9_(k, k, ux, uy, h);
             } else {
                 const Real k[5] = {dT, Tr * ux, Tr * uy, c2 * dT - Tr * ux2, c2 * dT - Tr * uy2};
-                central_to_pop5_(k, ux, uy, h);
+                central_to_pop5_(k, k, ux, uy, h);
             }
 #pragma unroll
             for (int a = 0; a < QT; ++a) {
@@ -192,23 +195,23 @@ cudaError_t launch_reduce(const double *macro, double *uprev, long long N, int u
     return cudaGetLastError();
 }
 
-// ---- conversions ----
+// ---- conversions (ref: optional [Q][ny] values subtracted before storing, in FP64) ----
 template <typename Real, typename Store>
 __global__ void to_store_kernel(const double *__restrict__ src, Store *__restrict__ dst, int Q, int nx, int ny, int pitch,
-                                Real scale)
+                                Real scale, const double *__restrict__ ref)
 {
     const long long N = (long long)Q * nx * ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const long long q = i / ((long long)nx * ny), r = i - q * nx * ny;
         const int y = int(r / nx), x = int(r - (long long)y * nx);
-        Real v = Real(src[i]);
+        Real v = Real(ref ? src[i] - ref[q * ny + y] : src[i]);
         if constexpr (scaled_<Store>()) v *= scale;
         st_(dst + (q * ny + y) * (long long)pitch + x, v);
     }
 }
 template <typename Real, typename Store>
 __global__ void from_store_kernel(const Store *__restrict__ src, double *__restrict__ dst, int Q, int nx, int ny,
-                                  int pitch, Real iscale)
+                                  int pitch, Real iscale, const double *__restrict__ ref)
 {
     const long long N = (long long)Q * nx * ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
@@ -216,23 +219,25 @@ __global__ void from_store_kernel(const Store *__restrict__ src, double *__restr
         const int y = int(r / nx), x = int(r - (long long)y * nx);
         Real v = ld_<Real, Store>(src + (q * ny + y) * (long long)pitch + x);
         if constexpr (scaled_<Store>()) v *= iscale;
-        dst[i] = double(v);
+        dst[i] = ref ? double(v) + ref[q * ny + y] : double(v);
     }
 }
 template <typename Real, typename Store>
-cudaError_t launch_to_store(const double *src, Store *dst, int Q, int nx, int ny, int pitch, Real scale, cudaStream_t s)
+cudaError_t launch_to_store(const double *src, Store *dst, int Q, int nx, int ny, int pitch, Real scale,
+                            const double *ref, cudaStream_t s)
 {
     const long long N = (long long)Q * nx * ny;
     const int blocks = int((N + 255) / 256 < 8192 ? (N + 255) / 256 : 8192);
-    to_store_kernel<Real, Store><<<blocks, 256, 0, s>>>(src, dst, Q, nx, ny, pitch, scale);
+    to_store_kernel<Real, Store><<<blocks, 256, 0, s>>>(src, dst, Q, nx, ny, pitch, scale, ref);
     return cudaGetLastError();
 }
 template <typename Real, typename Store>
-cudaError_t launch_from_store(const Store *src, double *dst, int Q, int nx, int ny, int pitch, Real iscale, cudaStream_t s)
+cudaError_t launch_from_store(const Store *src, double *dst, int Q, int nx, int ny, int pitch, Real iscale,
+                              const double *ref, cudaStream_t s)
 {
     const long long N = (long long)Q * nx * ny;
     const int blocks = int((N + 255) / 256 < 8192 ? (N + 255) / 256 : 8192);
-    from_store_kernel<Real, Store><<<blocks, 256, 0, s>>>(src, dst, Q, nx, ny, pitch, iscale);
+    from_store_kernel<Real, Store><<<blocks, 256, 0, s>>>(src, dst, Q, nx, ny, pitch, iscale, ref);
     return cudaGetLastError();
 }
 
@@ -267,8 +272,10 @@ LBM_INST_INIT(float, __half, 9, 9)
 #undef LBM_INST_INIT
 
 #define LBM_INST_CONV(R, S)                                                                                \
-    template cudaError_t launch_to_store<R, S>(const double *, S *, int, int, int, int, R, cudaStream_t); \
-    template cudaError_t launch_from_store<R, S>(const S *, double *, int, int, int, int, R, cudaStream_t);
+    template cudaError_t launch_to_store<R, S>(const double *, S *, int, int, int, int, R, const double *,        \
+                                               cudaStream_t);                                                   \
+    template cudaError_t launch_from_store<R, S>(const S *, double *, int, int, int, int, R, const double *,      \
+                                                 cudaStream_t);
 LBM_INST_CONV(double, double)
 LBM_INST_CONV(float, float)
 LBM_INST_CONV(float, __half)

@@ -4,13 +4,18 @@
 // central-moment collisions in closed form.
 //
 // Variables carried (exact affine changes of the paper's variables):
-//   f          phase-field populations, as in Sec. 4.1;
+//   f - r(y)   phase-field populations (Sec. 4.1) minus those of a reference state r that
+//              depends on the row only: the flat tanh interface of width W at y = b, at
+//              rest, at its central-moment equilibrium (first moment M_phi theta, the
+//              normal pointing up);
 //   g - w p0   flow populations minus the rest weights times p0 = rho_A c^2 (Sec. 4.2);
 //   h - w Tr   energy populations minus the rest weights times T_ref (Sec. 4.3);
 //   dp = p - p0.
-// The velocity is ~1e-5 of p, so the deviations keep round-off far below the signal in
-// FP64 and FP32 alike.  Equilibria are the printed ones minus the central moments of
-// the subtracted rest state, written without cancellation.
+// The velocity is ~1e-5 of p and the interface tilt that drives it is a ~1e-5 change of
+// phi ~ 1, so carrying deviations keeps round-off far below the signal: phi - phi0(y),
+// its gradient, the normal's n_y - 1 and the collision's output are formed from small
+// numbers and never from differences of O(1) ones.  Equilibria are the printed ones
+// minus the central moments of the subtracted reference, written without cancellation.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -63,6 +68,15 @@ template <typename Real, typename Store> struct StepArgs {
     const Real *dp_in;              // p - p0 of the previous step [ny][pitch]
     Real *dp_out;
     const Real *twall;              // [3][nx]: T_w - T_ref at x - 1/2, x, x + 1/2 (bottom wall)
+    // per-row tables of the phase-field reference, [RT_N][ny + 2], row r at index r + 1:
+    // phi0(r) = sum_a r_a(r), dR(r) = (sum of the pulled reference populations) - phi0(r)
+    // (as high and low parts in FP32), the normal's reference gradient d_y phi0 (r = -1 ..
+    // ny, ghost rows mirrored), theta(phi0(r)) and the first-moment constant
+    // c01(r) = (1 - omega_phi) Ry(r) + omega_phi M_phi theta(phi0(r)) - t01(r), Ry the first
+    // y moment of the pulled reference populations and t01 that of r itself
+    const Real *rtab;
+    const double *phi0;             // [ny]: phi0 in FP64 (field export)
+    const double *fref;             // [QF][ny]: the reference populations r_a(y) in FP64
     double *macro;                  // optional [5][ny][nx]: phi, u, v, T, dp
     // per-population plane base pointers (plane a of lattice X starts at X_in + a * plane)
     const Store *fi[9], *gi[9], *hi[9];
@@ -73,6 +87,9 @@ template <typename Real, typename Store> struct StepArgs {
     unsigned int *fault;            // set to nonzero by a CTA that abandoned the step
     unsigned int tx_extra;          // bytes each stage expects beyond its copies: 0 (test hook)
 };
+
+// rows of StepArgs::rtab
+enum { RT_PHI0 = 0, RT_DR = 1, RT_GREF = 2, RT_TH0 = 3, RT_C01 = 4, RT_DRLO = 5, RT_N = 6 };
 
 // ---- storage conversion ----
 template <typename Real, typename Store>
@@ -139,24 +156,72 @@ __device__ __forceinline__ void unit_normal_(Real gx, Real gy, Real g2min, Real 
     }
 }
 
+// Reciprocal: IEEE in FP64; in FP32 the hardware approximation (about 1 ulp): the
+// operands are densities, relaxation rates and gradient norms of order one or above the
+// normal's threshold, and FP32 storage dominates the error budget.
+template <typename Real>
+__device__ __forceinline__ Real rcp_(Real x)
+{
+    if constexpr (std::is_same<Real, double>::value) {
+        return 1.0 / x;
+    } else {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+}
+
+// The unit normal n = grad phi / |grad phi| as (n_x, n_y - 1).  For an interface close to
+// the flat reference n_y is close to 1, so n_y - 1 = -g_x^2 / (|g| (|g| + g_y)) is formed
+// without cancellation; the stencils of div n take its differences.  n = 0 (n_y - 1 = -1)
+// where |grad phi|^2 <= g2min.
+template <typename Real>
+__device__ __forceinline__ void unit_normal_dev_(Real gx, Real gy, Real g2min, Real &nx, Real &my)
+{
+    const Real g2 = gx * gx + gy * gy;
+    if (g2 > g2min) {
+        Real m, im;
+        if constexpr (std::is_same<Real, double>::value) {
+            m = sqrt(g2);
+            im = 1.0 / m;
+        } else {
+            im = rsqrtf(g2);
+            m = g2 * im;
+        }
+        nx = gx * im;
+        my = gy > Real(0) ? -gx * nx * rcp_(m + gy) : gy * im - Real(1);
+    } else {
+        nx = Real(0);
+        my = Real(-1);
+    }
+}
+
 // ---- App. B: central moments -> populations, F(-u) then P^-1 (D2Q9).
 // Moment order 00, 10, 01, 20, 02, 11, 21, 12, 22. ----
-template <typename Real>
-__device__ __forceinline__ void central_to_pop9_(const Real k[9], Real ux, Real uy, Real g[9])
+// dk: the central moments minus those of a reference at u = 0 (whose raw moments they
+// are), k: the full central moments.  Raw moments r = F(-u) k = k + (F(-u) - I) k, so the
+// deviation of r from the reference is dk + (F(-u) - I) k: every term of the second part
+// carries a velocity factor.  With dk = k this is the plain map.
+// REST_LAST: the rest population is formed last as r00 - (sum of the others), so that the
+// populations sum to the conserved zeroth moment up to one rounding of a small number
+// (measured on a float32 conduction lattice: the T error after 2000 steps falls from
+// 2.9e-6 to 1.8e-7, the level of float32 storage alone); used for the conserved scalar
+// lattices (phi, T).
+template <typename Real, bool REST_LAST = false>
+__device__ __forceinline__ void central_to_pop9_(const Real dk[9], const Real k[9], Real ux, Real uy, Real g[9])
 {
     const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
-    const Real r00 = k[0];
-    const Real r10 = k[1] + ux * k[0];
-    const Real r01 = k[2] + uy * k[0];
-    const Real r20 = k[3] + Real(2) * ux * k[1] + ux2 * k[0];
-    const Real r02 = k[4] + Real(2) * uy * k[2] + uy2 * k[0];
-    const Real r11 = k[5] + uy * k[1] + ux * k[2] + uxy * k[0];
-    const Real r21 = k[6] + Real(2) * ux * k[5] + uy * k[3] + ux2 * k[2] + Real(2) * uxy * k[1] + ux2 * uy * k[0];
-    const Real r12 = k[7] + Real(2) * uy * k[5] + ux * k[4] + uy2 * k[1] + Real(2) * uxy * k[2] + ux * uy2 * k[0];
-    const Real r22 = k[8] + Real(2) * ux * k[7] + Real(2) * uy * k[6] + ux2 * k[4] + uy2 * k[3] +
+    const Real r00 = dk[0];
+    const Real r10 = dk[1] + ux * k[0];
+    const Real r01 = dk[2] + uy * k[0];
+    const Real r20 = dk[3] + Real(2) * ux * k[1] + ux2 * k[0];
+    const Real r02 = dk[4] + Real(2) * uy * k[2] + uy2 * k[0];
+    const Real r11 = dk[5] + uy * k[1] + ux * k[2] + uxy * k[0];
+    const Real r21 = dk[6] + Real(2) * ux * k[5] + uy * k[3] + ux2 * k[2] + Real(2) * uxy * k[1] + ux2 * uy * k[0];
+    const Real r12 = dk[7] + Real(2) * uy * k[5] + ux * k[4] + uy2 * k[1] + Real(2) * uxy * k[2] + ux * uy2 * k[0];
+    const Real r22 = dk[8] + Real(2) * ux * k[7] + Real(2) * uy * k[6] + ux2 * k[4] + uy2 * k[3] +
                      Real(4) * uxy * k[5] + Real(2) * uxy * uy * k[1] + Real(2) * uxy * ux * k[2] + ux2 * uy2 * k[0];
     const Real h = Real(0.5), q = Real(0.25);
-    g[0] = r00 - r20 - r02 + r22;
     g[1] = h * (r10 + r20 - r12 - r22);
     g[2] = h * (r01 + r02 - r21 - r22);
     g[3] = h * (-r10 + r20 + r12 - r22);
@@ -165,23 +230,27 @@ __device__ __forceinline__ void central_to_pop9_(const Real k[9], Real ux, Real 
     g[6] = q * (-r11 + r21 - r12 + r22);
     g[7] = q * (r11 - r21 - r12 + r22);
     g[8] = q * (-r11 - r21 + r12 + r22);
+    if constexpr (REST_LAST)
+        g[0] = r00 - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
+    else
+        g[0] = r00 - r20 - r02 + r22;
 }
 
 // D2Q5 analogue: basis 1, e_x, e_y, e_x^2, e_y^2 (the first five rows of F(-u)).
-template <typename Real>
-__device__ __forceinline__ void central_to_pop5_(const Real k[5], Real ux, Real uy, Real f[5])
+template <typename Real, bool REST_LAST = false>
+__device__ __forceinline__ void central_to_pop5_(const Real dk[5], const Real k[5], Real ux, Real uy, Real f[5])
 {
-    const Real r00 = k[0];
-    const Real r10 = k[1] + ux * k[0];
-    const Real r01 = k[2] + uy * k[0];
-    const Real r20 = k[3] + Real(2) * ux * k[1] + ux * ux * k[0];
-    const Real r02 = k[4] + Real(2) * uy * k[2] + uy * uy * k[0];
+    const Real r00 = dk[0];
+    const Real r10 = dk[1] + ux * k[0];
+    const Real r01 = dk[2] + uy * k[0];
+    const Real r20 = dk[3] + Real(2) * ux * k[1] + ux * ux * k[0];
+    const Real r02 = dk[4] + Real(2) * uy * k[2] + uy * uy * k[0];
     const Real h = Real(0.5);
-    f[0] = r00 - r20 - r02;
     f[1] = h * (r10 + r20);
     f[2] = h * (r01 + r02);
     f[3] = h * (r20 - r10);
     f[4] = h * (r02 - r01);
+    f[0] = REST_LAST ? r00 - ((f[1] + f[3]) + (f[2] + f[4])) : r00 - r20 - r02;
 }
 
 template <int Q, typename Real>
@@ -196,22 +265,34 @@ __device__ __forceinline__ void raw_first_(const Real *p, Real &m10, Real &m01)
     }
 }
 
-// ---- Sec. 4.1 phase-field collision: first central moments relax at omega_phi towards
-// M_phi theta n, the rest take their equilibria (phi, c^2 phi, c^2 phi, 0, 0, 0, c^4 phi).
+// ---- Sec. 4.1 phase-field collision in deviation variables.  The first central moments
+// relax at omega_phi towards M_phi theta n, the rest take their equilibria (phi, c^2 phi,
+// c^2 phi, 0, 0, 0, c^4 phi).  In: s = pulled f - r (r the reference populations at the
+// rows they were pulled from), dphi = phi - phi0(y), phi, u, the normal (n_x, n_y - 1),
+// theta0 = theta(phi0(y)) and dth = theta(phi) - theta0, c01 (see StepArgs::rtab).  Out:
+// s = post-collision f - r(y).  With Rx = sum e_x r(pulled) = 0 (the reference is even
+// in x) the pre-collision first central moments are k10 = sum e_x s - u_x phi and
+// k01 = sum e_y s + Ry(y) - u_y phi; the reference's own post-collision first moments are
+// (0, t01(y)), t01 ~ M_phi theta0. ----
 template <int Q, typename Real>
-__device__ __forceinline__ void collide_phase_(Real *f, Real phi, Real ux, Real uy, Real mx, Real my, Real om)
+__device__ __forceinline__ void collide_phase_dev_(Real *s, Real dphi, Real phi, Real ux, Real uy, Real nx, Real my,
+                                                   Real th0, Real dth, Real c01, Real M, Real om)
 {
     Real m10, m01;
-    raw_first_<Q>(f, m10, m01);
-    const Real k10 = m10 - ux * phi, k01 = m01 - uy * phi;
-    const Real t10 = k10 + om * (mx - k10), t01 = k01 + om * (my - k01);
-    const Real c2p = phi * Real(1.0 / 3.0);
+    raw_first_<Q>(s, m10, m01);
+    const Real w1 = Real(1) - om, oM = om * M;
+    const Real t10 = w1 * (m10 - ux * phi) + oM * (th0 + dth) * nx;
+    const Real dt01 = w1 * (m01 - uy * phi) + oM * (th0 * my + dth * (Real(1) + my)) + c01;
+    const Real t01 = M * th0 + dt01;
+    const Real c2 = Real(1.0 / 3.0), c2d = c2 * dphi, c2p = c2 * phi;
     if constexpr (Q == 9) {
+        const Real dk[9] = {dphi, t10, dt01, c2d, c2d, Real(0), Real(0), Real(0), dphi * Real(1.0 / 9.0)};
         const Real k[9] = {phi, t10, t01, c2p, c2p, Real(0), Real(0), Real(0), phi * Real(1.0 / 9.0)};
-        central_to_pop9_(k, ux, uy, f);
+        central_to_pop9_<Real, true>(dk, k, ux, uy, s);
     } else {
+        const Real dk[5] = {dphi, t10, dt01, c2d, c2d};
         const Real k[5] = {phi, t10, t01, c2p, c2p};
-        central_to_pop5_(k, ux, uy, f);
+        central_to_pop5_<Real, true>(dk, k, ux, uy, s);
     }
 }
 
@@ -237,10 +318,10 @@ __device__ __forceinline__ void collide_energy_(Real *h, Real dT, Real ux, Real 
                            Tr * (c2 + ux2) * uy,
                            Tr * (c2 + uy2) * ux,
                            Real(1.0 / 9.0) * dT - Tr * (c2 * (ux2 + uy2) + ux2 * uy2)};
-        central_to_pop9_(k, ux, uy, h);
+        central_to_pop9_<Real, true>(k, k, ux, uy, h);
     } else {
         const Real k[5] = {dT, t10, t01, c2 * dT - Tr * ux2, c2 * dT - Tr * uy2};
-        central_to_pop5_(k, ux, uy, h);
+        central_to_pop5_<Real, true>(k, k, ux, uy, h);
     }
 }
 
@@ -288,7 +369,7 @@ __device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real u
     k[6] = q21;
     k[7] = q12;
     k[8] = q22;
-    central_to_pop9_(k, ux, uy, g);
+    central_to_pop9_(k, k, ux, uy, g);
 }
 
 }  // namespace lbm

@@ -35,13 +35,14 @@ cudaError_t launch_reduce(const double *macro, double *uprev, long long N, int u
                           int nblk, double *result, cudaStream_t s);
 int reduce_blocks();
 
-// [Q][ny][nx] doubles <-> [Q][ny][pitch] storage (value * scale stored)
+// [Q][ny][nx] doubles <-> [Q][ny][pitch] storage ((value - ref[q][y]) * scale stored; ref
+// may be NULL)
 template <typename Real, typename Store>
 cudaError_t launch_to_store(const double *src, Store *dst, int Q, int nx, int ny, int pitch, Real scale,
-                            cudaStream_t s);
+                            const double *ref, cudaStream_t s);
 template <typename Real, typename Store>
 cudaError_t launch_from_store(const Store *src, double *dst, int Q, int nx, int ny, int pitch, Real iscale,
-                              cudaStream_t s);
+                              const double *ref, cudaStream_t s);
 // macro plane -> device array of float or double
 cudaError_t launch_export(const double *src, void *dst, long long N, int to_float, cudaStream_t s);
 

@@ -2,7 +2,8 @@
 // method (arXiv 2210.07501, Sec. 4.1-4.3) for sm_103a.
 //
 // Per step and node: pull f and h (Sec. 4.1, 4.3 streaming with the Sec. 5.1 wall rules)
-// and form phi = sum f and T - T_ref = sum h; stage phi (radius 2), sigma(T) - sigma0 and
+// and form phi = sum f and T - T_ref = sum h (phi as its deviation from the row's
+// reference profile phi0, see lbm_device.cuh); stage phi (radius 2), sigma(T) - sigma0 and
 // p^{n-1} - p0 (radius 1) in shared memory (ghost rows: phi, p mirrored; T = 2 T_w - T_adj);
 // form the unit normal n = grad phi / |grad phi|; then the curvature term div n, grad sigma,
 // grad p, the CSF force with delta_s = 1.5 W |grad phi|^2 (Sec. 3), the pressure force
@@ -18,9 +19,10 @@ namespace lbm {
 
 // ---- row-marching sliding window ------------------------------------------------------
 // One CTA of TX threads owns a TX-column strip and walks up a segment of rows.  Shared
-// memory holds rings of the last rows: phi (8 rows, radius-2 halo columns), the pair
-// (sigma - sigma0, p - p0) and the unit normal (4 rows, radius-1 halo columns).  For output
-// row y the CTA adds phi of row y + 2 (from f pulled there, kept in registers until row y
+// memory holds rings of the last rows: phi - phi0 (8 rows, radius-2 halo columns), the
+// pair (sigma - sigma0, p - p0) and the unit normal as (n_x, n_y - 1) (4 rows, radius-1
+// halo columns).  For output
+// row y the CTA adds phi of row y + 3 (from f pulled there, kept in registers until row y
 // collides), sigma and p of row y + 1 (from h pulled there, kept one row), the normals of
 // row y + 1, and then collides row y.  The population rows come from a ring of D stages
 // in shared memory filled by bulk copies D - 1 rows ahead (below); the first rows of a
@@ -37,20 +39,6 @@ __device__ __forceinline__ void grad3_(const Real *rm, const Real *r0, const Rea
     const Real ne = rp[c + 1], nw = rp[c - 1], se = rm[c + 1], sw = rm[c - 1];
     gx = c1 * (r0[c + 1] - r0[c - 1]) + c2 * ((ne - nw) + (se - sw));
     gy = c1 * (rp[c] - rm[c]) + c2 * ((ne - se) + (nw - sw));
-}
-
-template <typename Real>
-__device__ __forceinline__ Real rcp_(Real x)
-{
-    if constexpr (std::is_same<Real, double>::value) {
-        return 1.0 / x;
-    } else {
-        // hardware reciprocal (about 1 ulp): the operands are densities and relaxation
-        // rates of order one, and FP32 storage dominates the error budget
-        float r;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-        return r;
-    }
 }
 
 // Loads of one row for the pull: populations of one lattice (plane base pointers `pl`,
@@ -91,7 +79,7 @@ __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int
 // The population rows a CTA pulls from are copied into shared memory by the bulk-copy (TMA)
 // engine, D - 1 output rows ahead of the row being collided: the loads hold no registers
 // and each SM keeps several rows of every plane in flight.  Stage k of a CTA serves output
-// row y = y0 + k and holds the source rows of f pulled at row y + 2, of h pulled at y + 1
+// row y = y0 + k and holds the source rows of f pulled at row y + 3, of h pulled at y + 1
 // and of g pulled at y (after the wall rules: the reflected or reversed plane's row at a
 // wall), and dp of row y + 1, each over the strip's columns plus a halo on both sides.
 // Bulk copies move 16-byte aligned spans; columns that wrap around the periodic x edge, or
@@ -203,15 +191,19 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     constexpr int PX = TX + 4, SX = TX + 2, NT = TX + 32;
     constexpr int D = G::D, HS = G::HS, HD = G::HD, RS = G::RS, RD = G::RD, NP = G::NP;
     constexpr int CS = 16 / (int)sizeof(Store), CD = 16 / (int)sizeof(Real);   // elements per 16 bytes
-    __shared__ Real s_phi[8][PX];
+    __shared__ Real s_phi[8][PX];   // phi - phi0
     __shared__ R2 s_sp[4][SX];   // (sigma - sigma0, p - p0)
-    __shared__ R2 s_n[4][SX];    // unit normal
+    __shared__ R2 s_n[4][SX];    // unit normal (n_x, n_y - 1)
     __shared__ int s_abort;
     extern __shared__ __align__(128) unsigned char s_dyn[];
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(s_dyn + D * G::BYTES);
 
     const int nx = A.nx, ny = A.ny, pitch = A.pitch;
     const Phys<Real> &P = A.P;
+    // reference-profile row tables (row r at r + 1; CTA-uniform loads)
+    const Real *t_phi0 = A.rtab + 1, *t_dR = A.rtab + (ny + 2) * RT_DR + 1, *t_gref = A.rtab + (ny + 2) * RT_GREF + 1;
+    const Real *t_th0 = A.rtab + (ny + 2) * RT_TH0 + 1, *t_c01 = A.rtab + (ny + 2) * RT_C01 + 1;
+    const Real *t_dRlo = A.rtab + (ny + 2) * RT_DRLO + 1;
     const int tid = threadIdx.x;
     const int x0 = bx * TX;
     const int y0 = by * seg;
@@ -342,11 +334,15 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, xh, xhm, xhp, A.ish, A.twall, P.dTcold, h);
         dp = A.dp_in[gy * pitch + xh];
     };
+    // phi - phi0 of row r (ghost rows: of the mirrored row) from the pulled deviations
     auto put_phi = [&](int r, const Real *f) {
-        Real phi = f[0];
+        Real dphi = f[0];
 #pragma unroll
-        for (int a = 1; a < QF; ++a) phi += f[a];
-        s_phi[r & 7][cf + 2] = phi;
+        for (int a = 1; a < QF; ++a) dphi += f[a];
+        const int gy = mirror_row_(r, ny);
+        if constexpr (std::is_same<Real, double>::value) dphi += __ldg(t_dR + gy);
+        else dphi = (dphi + __ldg(t_dRlo + gy)) + __ldg(t_dR + gy);
+        s_phi[r & 7][cf + 2] = dphi;
     };
     auto put_sig = [&](int r, const Real *h, Real dp) {
         Real dT = h[0];
@@ -359,11 +355,12 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         v.y = dp;
         s_sp[r & 3][ch + 1] = v;
     };
+    // grad phi = grad (phi - phi0) + (0, d_y phi0); the normal as (n_x, n_y - 1)
     auto put_n = [&](int r) {
         Real gx, gy;
         R2 n;
         grad3_(s_phi[(r - 1) & 7], s_phi[r & 7], s_phi[(r + 1) & 7], ch + 2, gx, gy);
-        unit_normal_(gx, gy, P.g2min, n.x, n.y);
+        unit_normal_dev_(gx, gy + __ldg(t_gref + r), P.g2min, n.x, n.y);
         s_n[r & 3][ch + 1] = n;
     };
     // After a wait gave up: flag the fault, let every copy this CTA started land, return.
@@ -458,9 +455,11 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         if (xin) {
             const int c = tid + 2, s = tid + 1;
             const Real *pm = s_phi[(y - 1) & 7], *p0 = s_phi[y & 7], *pp = s_phi[(y + 1) & 7];
-            const Real phi = p0[c];
+            const Real dphi = p0[c], phi_ref = __ldg(t_phi0 + y), th0 = __ldg(t_th0 + y);
+            const Real phi = phi_ref + dphi;
             Real gpx, gpy;
             grad3_(pm, p0, pp, c, gpx, gpy);
+            gpy += __ldg(t_gref + y);
             const Real g2 = gpx * gpx + gpy * gpy;
             const R2 *nm = s_n[(y - 1) & 3], *n0 = s_n[y & 3], *np = s_n[(y + 1) & 3];
             const R2 *qm = s_sp[(y - 1) & 3], *q0 = s_sp[y & 3], *qp = s_sp[(y + 1) & 3];
@@ -475,7 +474,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real dsy = c1 * (qN.x - qS.x) + cd * ((qNE.x - qSE.x) + (qNW.x - qSW.x));
             const Real dpx = c1 * (qE.y - qW.y) + cd * ((qNE.y - qNW.y) + (qSE.y - qSW.y));
             const Real dpy = c1 * (qN.y - qS.y) + cd * ((qNE.y - qSE.y) + (qNW.y - qSW.y));
-            const Real nxv = nC.x, nyv = nC.y;
+            const Real nxv = nC.x, nyv = Real(1) + nC.y;
             Real dT = hq0[0];
 #pragma unroll
             for (int a = 1; a < QT; ++a) dT += hq0[a];
@@ -495,8 +494,10 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real dp = s0 + hf * (Fpx * ux + Fpy * uy);
             const Real om_nu = rcp_(Real(3) * (P.muA + phi * P.dmu) * irho + hf);
             const Real om_T = rcp_(Real(3) * (P.kA + phi * P.dk) * irho + hf);
-            const Real theta = P.W4 * phi * (Real(1) - phi);
-            collide_phase_<QF>(fq0, phi, ux, uy, P.Mphi * theta * nxv, P.Mphi * theta * nyv, P.omega_phi);
+            // theta(phi) - theta(phi0) = (4 / W) dphi (1 - 2 phi0 - dphi)
+            const Real dth = P.W4 * dphi * (Real(1) - Real(2) * phi_ref - dphi);
+            collide_phase_dev_<QF>(fq0, dphi, phi, ux, uy, nxv, nC.y, th0, dth, __ldg(t_c01 + y), P.Mphi,
+                                   P.omega_phi);
             collide_flow_(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy);
             collide_energy_<QT>(hq0, dT, ux, uy, P.T_ref, om_T);
             const int o = y * pitch + x;
@@ -525,7 +526,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             A.dp_out[o] = dp;
             if (A.macro) {
                 const long long N = (long long)nx * ny, m = (long long)y * nx + x;
-                A.macro[m] = double(phi);
+                A.macro[m] = A.phi0[y] + double(dphi);
                 A.macro[N + m] = double(ux);
                 A.macro[2 * N + m] = double(uy);
                 A.macro[3 * N + m] = double(P.T_ref) + double(dT);

@@ -12,14 +12,13 @@ At these coefficients the interface velocity is ~1e-7: FP64 storage (FP32 storag
 velocities down to ~1e-8 of the populations only).
 
 U_max is the largest |u| on the interface, taken as the mean of the two node rows that
-straddle it (y = b -/+ 1/2); the closed-form solution of Sec. 3 is read off the same way.
-Every step of the sweep runs in the CUDA library.
+straddle it (y = b -/+ 1/2).  Every step of the sweep runs in the CUDA library; comparisons
+with the closed-form solution of Sec. 3 are made by the callers that hold one.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import surrogate as S
 from .warmstart import steady_batch
 
 AB = (1.0 / 3.0, 1.0, 3.0)
@@ -63,10 +62,8 @@ def run(case_list: list, precision: str = "fp64", tol: float = 1e-6, max_steps: 
     fields, steps, conv, seconds = steady_batch(case_list, tol, max_steps, precision, stream=stream)
     out = []
     for c, f, n, ok in zip(case_list, fields, steps, conv):
-        _, u_cf, _ = S.closed_form(c["domain"], c["params"])
         out.append({"name": c["name"], "b": c["domain"]["b"], "params": c["params"], "steps": int(n),
-                    "converged": bool(ok), "U_lb": interface_u_max(f["u"], c["domain"]["b"]),
-                    "U_closed_form": interface_u_max(u_cf, c["domain"]["b"])})
+                    "converged": bool(ok), "U_lb": interface_u_max(f["u"], c["domain"]["b"])})
     return out, seconds
 
 
@@ -124,26 +121,15 @@ def run_deformation(M2_values=(0.1, 3.0, 5.0, 10.0, 20.0), precision: str = "fp3
     return out, seconds
 
 
-# ---- steady state of the 1024 x 256 channel against the closed form ----
+# ---- steady state of the 1024 x 256 channel ----
 # a = b = 128, W = 5, sigma2 = -2e-4, sigma1 in {0, 2e-5}, mu~ = k~ = 2, tau_b = 0.8.  The run
-# starts from the closed-form temperature (the slowest mode of the approach to steady state is
-# thermal) with the fluid at rest, and stops at r <= tol or max_steps.
+# starts from the caller's initial fields (e.g. a temperature close to the steady one: the
+# slowest mode of the approach to steady state from rest is thermal) and stops at r <= tol
+# or max_steps; it returns the steady fields and the interface velocity.
 
-def steady_vs_closed_form(cases: list, precision: str = "fp64", tol: float = 1e-8, max_steps: int = 1500000,
-                          stream=None) -> list:
-    init = [{"T": S.closed_form(c["domain"], c["params"])[0]} for c in cases]
+def steady(cases: list, init=None, precision: str = "fp64", tol: float = 1e-8, max_steps: int = 1500000,
+           stream=None) -> list:
     fields, steps, conv, seconds = steady_batch(cases, tol, max_steps, precision, init=init, stream=stream)
-    out = []
-    for c, f, n, ok in zip(cases, fields, steps, conv):
-        d, p = c["domain"], c["params"]
-        T_cf, u_cf, v_cf = S.closed_form(d, p)
-        b = d["b"]
-        j = int(round(b))
-        rel = lambda a, e: float(np.linalg.norm(a - e) / max(np.linalg.norm(e), 1e-300))
-        Ti = 0.5 * (f["T"][j - 1] + f["T"][j]) - p["T_ref"]
-        Ti_cf = 0.5 * (T_cf[j - 1] + T_cf[j]) - p["T_ref"]
-        out.append({"name": c["name"], "steps": int(n), "converged": bool(ok), "seconds": seconds,
-                    "U_lb": interface_u_max(f["u"], b), "U_closed_form": interface_u_max(u_cf, b),
-                    "T_interface_rel": rel(Ti, Ti_cf), "T_rel": rel(f["T"] - p["T_ref"], T_cf - p["T_ref"]),
-                    "u_rel": rel(f["u"], u_cf), "v_rel": rel(f["v"], v_cf), "fields": f})
-    return out
+    return [{"name": c["name"], "steps": int(n), "converged": bool(ok), "seconds": seconds,
+             "U_lb": interface_u_max(f["u"], c["domain"]["b"]), "fields": f}
+            for c, f, n, ok in zip(cases, fields, steps, conv)]

@@ -5,13 +5,16 @@
 2. Training: the surrogate (`Cnn`, hand-written CUDA kernels) learns parameters + heating
    profile -> steady phi, T - T_ref, u/U, v/U (see `surrogate`), with Adam on the mean
    squared error; data stays on the GPU.
-3. Evaluation on held-out channels: the LB solver started from the surrogate's temperature
+3. Evaluation on held-out channels: the LB solver started from the surrogate's prediction
    (warm) against the solver started from rest (cold, the plain method and the reference):
    steps and wall time to the tolerance, the surrogate's own error against the converged LB
-   fields, and the difference between the warm- and cold-started converged fields.
-   The warm start takes T only: the velocity follows T within a viscous time, and starting
-   it from the surrogate's (rougher) velocity costs more steps than it saves (measured;
-   reported as a variant, with the closed-form solution of Sec. 3 as another).
+   fields, and the difference between the warm- and cold-started converged fields.  The
+   warm start takes the predicted temperature and interface (phi); variants start from the
+   predicted temperature alone and from all four predicted fields, and the caller may add
+   starts of its own (`extra_starts`), e.g. a reference solution, run the same way.
+   The slowest part of the approach to steady state is the settling of the interface,
+   which the predicted phi shortens; the temperature alone shortens only the thermal
+   transient.
 """
 from __future__ import annotations
 
@@ -105,20 +108,25 @@ def plain_per_case(cases, tol, max_steps, precision="fp32", init=None, K=100, st
 
 
 def experiment(train_cases, test_cases, tol=1e-5, max_steps=60000, iters=2000, batch=16, lr=1e-3, seed=0,
-               precision="fp32", log_every=0, plain_cases=0):
+               precision="fp32", log_every=0, plain_cases=0, extra_starts=None, train_tol=None, train_max_steps=None,
+               K=100):
     """Full pipeline; returns a dict of measurements.  Runs on one dedicated stream, shared
-    by torch's tensor operations and the library's kernels."""
+    by torch's tensor operations and the library's kernels.  The training channels run to
+    train_tol / train_max_steps (default: tol / max_steps), the held-out ones to tol, with
+    K steps between residual checks.  extra_starts: optional {name: [initial fields per
+    test case]} run as further variants."""
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         return _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every,
-                           stream, plain_cases)
+                           stream, plain_cases, extra_starts, train_tol or tol, train_max_steps or max_steps, K)
 
 
 def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every, stream,
-                plain_cases):
+                plain_cases, extra_starts, train_tol, train_max_steps, K):
     t0 = time.perf_counter()
-    f_train, s_train, c_train, _ = steady_batch(train_cases, tol, max_steps, precision, stream=stream)
+    f_train, s_train, c_train, _ = steady_batch(train_cases, train_tol, train_max_steps, precision, K=K,
+                                                stream=stream)
     t_data = time.perf_counter() - t0
     X, Y = dataset(train_cases, f_train)
     scale = target_scale(Y)
@@ -132,28 +140,37 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
     t0 = time.perf_counter()
     P = predict(net, Xt, scale)
     t_pred = time.perf_counter() - t0
-    init = [S.fields_from_prediction(c["domain"], c["params"], p, use_velocity=False) for c, p in zip(test_cases, P)]
-    f_cold, s_cold, c_cold, t_cold = steady_batch(test_cases, tol, max_steps, precision, stream=stream)
-    f_warm, s_warm, c_warm, t_warm = steady_batch(test_cases, tol, max_steps, precision, init=init, stream=stream)
+    init = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True) for c, p in zip(test_cases, P)]
+    f_cold, s_cold, c_cold, t_cold = steady_batch(test_cases, tol, max_steps, precision, K=K, stream=stream)
+    f_warm, s_warm, c_warm, t_warm = steady_batch(test_cases, tol, max_steps, precision, init=init, K=K,
+                                                  stream=stream)
     net.close()
-    # variants: the surrogate's T, u and v; the closed-form solution alone (no network)
+    # variants: the surrogate's T alone; T, interface and velocity; the caller's starts
     variants = {}
-    for name, ini in (("surrogate_T_u_v", [S.fields_from_prediction(c["domain"], c["params"], p)
-                                           for c, p in zip(test_cases, P)]),
-                      ("closed_form_T_u_v", [S.closed_form_fields(c["domain"], c["params"]) for c in test_cases]),
-                      ("closed_form_T", [{"T": S.closed_form_fields(c["domain"], c["params"])["T"]}
-                                         for c in test_cases])):
-        _, sv, cv, tv = steady_batch(test_cases, tol, max_steps, precision, init=ini, stream=stream)
+    starts = [("surrogate_T", [S.fields_from_prediction(c["domain"], c["params"], p)
+                               for c, p in zip(test_cases, P)]),
+              ("surrogate_T_phi_u_v", [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True,
+                                                                use_velocity=True) for c, p in zip(test_cases, P)])]
+    starts += list((extra_starts or {}).items())
+    for name, ini in starts:
+        fv, sv, cv, tv = steady_batch(test_cases, tol, max_steps, precision, init=ini, K=K, stream=stream)
         bv = np.flatnonzero(cv & c_cold)
         variants[name] = {"steps_mean": float(sv.mean()), "converged": int(cv.sum()), "seconds": tv,
+                          "steps": sv.tolist(),
                           "steps_mean_on_cold_converged": float(sv[bv].mean()) if bv.size else None,
                           "cold_steps_mean_same_cases": float(s_cold[bv].mean()) if bv.size else None,
-                          "fewer_steps_cases": int(np.sum(sv < s_cold))}
+                          "fewer_steps_cases": int(np.sum(sv < s_cold)),
+                          "final_vs_cold_rel_l2": {k: float(np.mean([rel_l2(fv[i][k], f_cold[i][k]) for i in bv]))
+                                                   if bv.size else None for k in ("phi", "u", "v", "T")}}
     # the surrogate's own error against the converged cold-start LB fields (the reference)
-    pred_fields = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True) for c, p in zip(test_cases, P)]
-    sur_err = {k: float(np.mean([rel_l2(i[k], f[k]) if k != "T" else
-                                 rel_l2(i[k] - c["params"]["T_ref"], f[k] - c["params"]["T_ref"])
-                                 for i, f, c in zip(pred_fields, f_cold, test_cases)])) for k in FIELDS}
+    pred_fields = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True, use_velocity=True)
+                   for c, p in zip(test_cases, P)]
+    # (phi: of its departure from the flat profile; T: of T - T_ref)
+    def _err(k, i, f, c):
+        base = S.phi_flat(c["domain"]) if k == "phi" else (c["params"]["T_ref"] if k == "T" else 0.0)
+        return rel_l2(i[k] - base, f[k] - base)
+    sur_err = {k: float(np.mean([_err(k, i, f, c) for i, f, c in zip(pred_fields, f_cold, test_cases)]))
+               for k in FIELDS}
     # warm vs cold converged fields, on the channels both runs brought to the tolerance
     both = np.flatnonzero(c_warm & c_cold)
     wc = {k: float(np.mean([rel_l2(f_warm[i][k], f_cold[i][k]) for i in both])) if both.size else None
@@ -161,13 +178,14 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
     plain = None
     if plain_cases:
         n = min(plain_cases, len(test_cases))
-        t_plain, s_plain = plain_per_case(test_cases[:n], tol, max_steps, precision, stream=stream)
+        t_plain, s_plain = plain_per_case(test_cases[:n], tol, max_steps, precision, K=K, stream=stream)
         plain = {"cases": n, "seconds": t_plain, "steps_mean": float(s_plain.mean()),
                  "same_steps_as_cold_batch": bool(np.array_equal(s_plain, s_cold[:n]))}
     return {
         "plain_per_case_cold": plain,
         "train_cases": len(train_cases), "test_cases": len(test_cases), "grid": [int(H), int(W)],
-        "tol": tol, "max_steps": max_steps, "precision": precision,
+        "tol": tol, "max_steps": max_steps, "precision": precision, "check_interval": K,
+        "train_tol": train_tol, "train_max_steps": train_max_steps,
         "data_seconds": t_data, "train_converged": int(c_train.sum()),
         "train_iters": iters, "batch": batch, "train_seconds": t_train,
         "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-20:])),

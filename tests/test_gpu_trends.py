@@ -33,8 +33,7 @@ def test_u_max_trends_match_closed_form():
         ua = analytic_u_max(c)
         ratios[r["name"]] = r["U_lb"] / ua
         print(f"{r['name']:32s} steps {r['steps']:6d} conv {r['converged']} U_lb {r['U_lb']:.4e} "
-              f"U_cf {r['U_closed_form']:.4e} analytic {ua:.4e} ratio {r['U_lb'] / ua:.3f}")
-        assert abs(r["U_closed_form"] - ua) <= 1e-9 * ua          # the product's closed form = the oracle's
+              f"analytic {ua:.4e} ratio {r['U_lb'] / ua:.3f}")
     # LB vs the sharp-interface closed form at W = 5 on 200 x 100: measured 0.82 (k~ = 1/4)
     # .. 0.88 (base) .. 1.07 (k~ = 4); the diffuse interface costs ~10 %, as the oracle's own
     # Marangoni pin shows (20 % at 64 x 32, halving under refinement)

@@ -28,6 +28,12 @@ MUTATIONS = {
                        "matching_principle"),
     "source_11": ("s[5] = c2 * (Fpx * uy + Fpy * ux) + ux * uy * G;", "s[5] = c2 * (Fpx * ux + Fpy * uy) + ux * uy * G;",
                   "two_layer_poiseuille"),
+    "source_20_factor": ("s[3] = 2.0 * c2 * Fpx * ux + (ux * ux + c2) * G;", "s[3] = c2 * Fpx * ux + (ux * ux + c2) * G;",
+                         "continuous_source"),
+    "source_02_component": ("s[4] = 2.0 * c2 * Fpy * uy + (uy * uy + c2) * G;",
+                            "s[4] = 2.0 * c2 * Fpy * uy + (ux * ux + c2) * G;", "continuous_source"),
+    "source_11_gamma_term": ("s[5] = c2 * (Fpx * uy + Fpy * ux) + ux * uy * G;", "s[5] = c2 * (Fpx * uy + Fpy * ux);",
+                             "continuous_source"),
     "shift_sign": ("ipow(-ux, m - p) * ipow(-uy, n - q);", "ipow(ux, m - p) * ipow(-uy, n - q);", "central_moment_shift"),
     "specular_as_bounce_back": ("int am = find_dir(o->Qf, EX[a], -EY[a]);", "int am = find_dir(o->Qf, -EX[a], -EY[a]);",
                                 "streaming_routes"),

@@ -165,6 +165,51 @@ def test_flow_source_injects_pressure_and_force(oracle_mod):
         assert np.allclose(r1[1:3] - r[1:3], C2 * Ft, atol=1e-18, rtol=0)
 
 
+def _continuous_source_central(u, Fp, Ft, order=12):
+    """Central moments (orders 00 .. 22, App. B order) of the continuous source of the
+    pressure-based formulation (Sec. 4.2, incompressible transformation):
+        S(xi) = (xi - u) . [ F_t G(xi; u) + F_p (G(xi; u) - G(xi; 0)) ],
+    G(xi; m) the unit Gaussian of variance c^2 centred at m: the force term of the
+    continuous Boltzmann equation for g = c^2 f + phi_p G(xi; 0).  Integrated by tensor
+    Gauss-Hermite quadrature, exact for these polynomial-times-Gaussian integrands."""
+    x, w = np.polynomial.hermite.hermgauss(order)
+    s = np.sqrt(2.0 * C2)
+    out = np.zeros(9)
+    for centre, Fcoef in ((u, Ft + Fp), (np.zeros(2), -Fp)):
+        X = centre[0] + s * x[:, None]
+        Y = centre[1] + s * x[None, :]
+        Wt = (w[:, None] * w[None, :]) / np.pi
+        proj = (X - u[0]) * Fcoef[0] + (Y - u[1]) * Fcoef[1]
+        for k, (m, n) in enumerate(MOM):
+            out[k] += np.sum(Wt * proj * (X - u[0]) ** m * (Y - u[1]) ** n)
+    return out
+
+
+def test_flow_source_central_moments_match_continuous_source(oracle_mod):
+    """The source's central moments sigma_mn of Sec. 4.2 (sigma_00 = Gamma, sigma_10,
+    sigma_01, sigma_20, sigma_02, sigma_11), read off the oracle's collision, equal the
+    central moments of the continuous forcing term through second order (the matching
+    principle); the third- and fourth-order ones are zero as printed.  With every rate 1
+    (omega_nu = 1) each post-collision central moment is equilibrium + sigma / 2, so the
+    difference between a forced and an unforced collision of the same state is sigma / 2."""
+    rng = np.random.default_rng(19)
+    for _ in range(8):
+        rho = rng.uniform(0.6, 1.8)
+        ux, uy = rng.uniform(-0.08, 0.08, 2)
+        Fp = rng.uniform(-1e-3, 1e-3, 2)
+        Ft = rng.uniform(-1e-3, 1e-3, 2)
+        dp = rng.uniform(-1e-3, 1e-3)
+        gdev = rng.uniform(-1e-3, 1e-3, 9)
+        forced = oracle_mod.collide_flow_site(gdev, rho, dp, ux, uy, Fp[0], Fp[1], Ft[0], Ft[1], 1.0)
+        free = oracle_mod.collide_flow_site(gdev, rho, dp, ux, uy, 0.0, 0.0, 0.0, 0.0, 1.0)
+        sigma = 2.0 * central(forced - free, ux, uy)
+        cont = _continuous_source_central(np.array([ux, uy]), Fp, Ft)
+        assert np.allclose(sigma[:6], cont[:6], atol=1e-17, rtol=1e-12), (sigma[:6], cont[:6])
+        assert np.allclose(sigma[6:], 0.0, atol=1e-17), sigma[6:]
+        # the matching is not vacuous: every second-order moment is present
+        assert min(abs(cont[3]), abs(cont[4]), abs(cont[5])) > 1e-8
+
+
 def test_flow_relaxation_rates_and_split(oracle_mod):
     """2s and all moments except 2d and 11 go to equilibrium; 2d and 11 relax at omega_nu."""
     rng = np.random.default_rng(17)
