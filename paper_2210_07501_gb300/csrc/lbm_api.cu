@@ -33,6 +33,7 @@ struct lbm_handle {
     void *dp[2];
     void *twall;            // Real [3][nx]
     void *rtab;             // Real [RT_N][ny + 2]: phase-field reference row tables
+    void *rowx;             // Real [ny][RX_N]: the same, grouped per output row
     double *phi0;           // [ny] reference phi profile
     double *fref;           // [Qf][ny] reference phase-field populations
     double *macro;          // [5][ny][nx]
@@ -107,6 +108,7 @@ template <typename Real, typename Store> static StepArgs<Real, Store> make_args(
     A.dp_out = (Real *)h->dp[dst];
     A.twall = (const Real *)h->twall;
     A.rtab = (const Real *)h->rtab;
+    A.rowx = (const Real *)h->rowx;
     A.phi0 = h->phi0;
     A.fref = h->fref;
     A.macro = macro;
@@ -176,6 +178,7 @@ static void free_all(lbm_handle *h)
     }
     if (h->twall) cudaFree(h->twall);
     if (h->rtab) cudaFree(h->rtab);
+    if (h->rowx) cudaFree(h->rowx);
     if (h->phi0) cudaFree(h->phi0);
     if (h->fref) cudaFree(h->fref);
     if (h->macro) cudaFree(h->macro);
@@ -320,13 +323,28 @@ static int build_phase_reference(lbm_handle *h)
         if (fabs(dR[j]) < fabs(dR[jmin])) jmin = j;
     }
     T(h->rsize == 8 ? RT_DR : RT_DRLO, jmin) -= tot.value();
+    // per output row: the values the row-marching kernel stages with the row
+    std::vector<double> rx((size_t)RX_N * ny, 0.0);
+    for (int j = 0; j < ny; ++j) {
+        double *o = rx.data() + (size_t)RX_N * j;
+        o[RX_PHI0] = T(RT_PHI0, j);
+        o[RX_TH0] = T(RT_TH0, j);
+        o[RX_C01] = T(RT_C01, j);
+        o[RX_GREF] = T(RT_GREF, j);
+        o[RX_DR3] = T(RT_DR, mirror(j + 3));
+        o[RX_DR3LO] = T(RT_DRLO, mirror(j + 3));
+        o[RX_GREF1] = T(RT_GREF, j + 1);
+    }
     cudaError_t e;
     if (h->rsize == 8) {
         e = cudaMemcpy(h->rtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->rowx, rx.data(), rx.size() * sizeof(double), cudaMemcpyHostToDevice);
     } else {
-        std::vector<float> tf(tab.size());
+        std::vector<float> tf(tab.size()), rf(rx.size());
         for (size_t i = 0; i < tab.size(); ++i) tf[i] = (float)tab[i];
+        for (size_t i = 0; i < rx.size(); ++i) rf[i] = (float)rx[i];
         e = cudaMemcpy(h->rtab, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->rowx, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemcpy(h->phi0, phi0.data(), ny * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->fref, r.data(), r.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -400,6 +418,7 @@ int lbm_create(const lbm_domain *domain, const lbm_params *params, void *stream,
     }
     ok = ok && cudaMalloc(&h->twall, 3 * (size_t)h->nx * h->rsize) == cudaSuccess;
     ok = ok && cudaMalloc(&h->rtab, (size_t)RT_N * (h->ny + 2) * h->rsize) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->rowx, (size_t)RX_N * h->ny * h->rsize) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->phi0, (size_t)h->ny * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->fref, (size_t)h->Qf * h->ny * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&h->macro, 5 * N * sizeof(double)) == cudaSuccess;

@@ -75,6 +75,9 @@ template <typename Real, typename Store> struct StepArgs {
     // c01(r) = (1 - omega_phi) Ry(r) + omega_phi M_phi theta(phi0(r)) - t01(r), Ry the first
     // y moment of the pulled reference populations and t01 that of r itself
     const Real *rtab;
+    // the same values regrouped per output row y, [ny][RX_N]: what the row-marching kernel
+    // needs at row y, staged in shared memory with the row's population copies
+    const Real *rowx;
     const double *phi0;             // [ny]: phi0 in FP64 (field export)
     const double *fref;             // [QF][ny]: the reference populations r_a(y) in FP64
     double *macro;                  // optional [5][ny][nx]: phi, u, v, T, dp
@@ -90,6 +93,9 @@ template <typename Real, typename Store> struct StepArgs {
 
 // rows of StepArgs::rtab
 enum { RT_PHI0 = 0, RT_DR = 1, RT_GREF = 2, RT_TH0 = 3, RT_C01 = 4, RT_DRLO = 5, RT_N = 6 };
+// fields of StepArgs::rowx for output row y: phi0(y), theta(phi0(y)), c01(y), d_y phi0(y),
+// dR of the mirrored row y + 3 (high, low), d_y phi0(y + 1), unused
+enum { RX_PHI0 = 0, RX_TH0 = 1, RX_C01 = 2, RX_GREF = 3, RX_DR3 = 4, RX_DR3LO = 5, RX_GREF1 = 6, RX_N = 8 };
 
 // ---- storage conversion ----
 template <typename Real, typename Store>

@@ -81,7 +81,8 @@ __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int
 // and each SM keeps several rows of every plane in flight.  Stage k of a CTA serves output
 // row y = y0 + k and holds the source rows of f pulled at row y + 3, of h pulled at y + 1
 // and of g pulled at y (after the wall rules: the reflected or reversed plane's row at a
-// wall), and dp of row y + 1, each over the strip's columns plus a halo on both sides.
+// wall), and dp of row y + 1, each over the strip's columns plus a halo on both sides, and
+// the row's values of the phase-field reference (StepArgs::rowx).
 // Bulk copies move 16-byte aligned spans; columns that wrap around the periodic x edge, or
 // lie past the last 16-byte boundary of a row, are copied element by element by all threads
 // (cp.async, or plain loads for 2-byte values), and each thread then arrives on the slot's
@@ -175,7 +176,9 @@ template <typename Real, typename Store, int QF, int QT, int TX> struct StageGeo
     static constexpr int HD = 4;                             // halo columns per side, dp plane
     static constexpr int RS = TX + 2 * HS, RD = TX + 2 * HD; // staged row lengths (16-byte multiples)
     static constexpr int NP = QF + QT + 9;                   // population planes per stage: f, h, g
-    static constexpr int BYTES = (NP * RS * (int)sizeof(Store) + RD * (int)sizeof(Real) + 127) / 128 * 128;
+    static constexpr int RXO = NP * RS * (int)sizeof(Store) + RD * (int)sizeof(Real);   // reference values
+    static constexpr int BYTES = (RXO + RX_N * (int)sizeof(Real) + 127) / 128 * 128;
+    static_assert(RXO % 16 == 0, "the staged reference values need a 16-byte aligned slot");
     static constexpr int RINGS = 8 * (TX + 4) * (int)sizeof(Real) + 16 * (TX + 2) * (int)sizeof(Real);
     // deepest ring that leaves room for march_ctas() CTAs per SM (228 KiB, 1 KiB reserved per CTA)
     static constexpr int BUDGET = 233472 / march_ctas<Real>() - 1024 - 128 - 16 - RINGS;
@@ -200,9 +203,9 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
 
     const int nx = A.nx, ny = A.ny, pitch = A.pitch;
     const Phys<Real> &P = A.P;
-    // reference-profile row tables (row r at r + 1; CTA-uniform loads)
-    const Real *t_phi0 = A.rtab + 1, *t_dR = A.rtab + (ny + 2) * RT_DR + 1, *t_gref = A.rtab + (ny + 2) * RT_GREF + 1;
-    const Real *t_th0 = A.rtab + (ny + 2) * RT_TH0 + 1, *t_c01 = A.rtab + (ny + 2) * RT_C01 + 1;
+    // reference-profile row tables for the first rows of a segment (row r at r + 1); the
+    // marching loop takes the same values from the staged rows
+    const Real *t_dR = A.rtab + (ny + 2) * RT_DR + 1, *t_gref = A.rtab + (ny + 2) * RT_GREF + 1;
     const Real *t_dRlo = A.rtab + (ny + 2) * RT_DRLO + 1;
     const int tid = threadIdx.x;
     const int x0 = bx * TX;
@@ -234,9 +237,11 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     const int n_edge = NP * nel_s + nel_d;
     const bool edge = n_edge > 0;                               // then every thread arrives too
     constexpr bool ASYNC = sizeof(Store) >= 4;
-    const uint32_t tx_bytes = uint32_t(NP * bspan * (int)sizeof(Store) + dspan * (int)sizeof(Real));
+    const uint32_t tx_bytes = uint32_t(NP * bspan * (int)sizeof(Store) + dspan * (int)sizeof(Real) +
+                                       RX_N * (int)sizeof(Real));
     auto stage_pop = [&](int sl) { return reinterpret_cast<Store *>(s_dyn + sl * G::BYTES); };
     auto stage_dp = [&](int sl) { return reinterpret_cast<Real *>(s_dyn + sl * G::BYTES + NP * RS * sizeof(Store)); };
+    auto stage_rx = [&](int sl) { return reinterpret_cast<const Real *>(s_dyn + sl * G::BYTES + G::RXO); };
 
     // source row of staged plane p for output row yy: f pulled at yy + 3, h at yy + 1, g at yy
     auto src_row = [&](int p, int yy) -> const Store * {
@@ -268,6 +273,9 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
                 if (dspan > 0)
                     bulk_g2s_(sd + doff, A.dp_in + (long long)mirror_row_(yy + 1, ny) * pitch + dlo,
                               dspan * sizeof(Real), &s_bar[sl]);
+            } else if (lane == NP + 1) {
+                bulk_g2s_(const_cast<Real *>(stage_rx(sl)), A.rowx + (long long)yy * RX_N, RX_N * sizeof(Real),
+                          &s_bar[sl]);
             }
         }
         if (edge) {
@@ -334,15 +342,19 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, xh, xhm, xhp, A.ish, A.twall, P.dTcold, h);
         dp = A.dp_in[gy * pitch + xh];
     };
-    // phi - phi0 of row r (ghost rows: of the mirrored row) from the pulled deviations
-    auto put_phi = [&](int r, const Real *f) {
+    // phi - phi0 of row r (ghost rows: of the mirrored row) from the pulled deviations and
+    // that row's dR (high and low parts)
+    auto put_phi_dr = [&](int r, const Real *f, Real dr, Real drlo) {
         Real dphi = f[0];
 #pragma unroll
         for (int a = 1; a < QF; ++a) dphi += f[a];
-        const int gy = mirror_row_(r, ny);
-        if constexpr (std::is_same<Real, double>::value) dphi += __ldg(t_dR + gy);
-        else dphi = (dphi + __ldg(t_dRlo + gy)) + __ldg(t_dR + gy);
+        if constexpr (std::is_same<Real, double>::value) dphi += dr;
+        else dphi = (dphi + drlo) + dr;
         s_phi[r & 7][cf + 2] = dphi;
+    };
+    auto put_phi = [&](int r, const Real *f) {
+        const int gy = mirror_row_(r, ny);
+        put_phi_dr(r, f, __ldg(t_dR + gy), __ldg(t_dRlo + gy));
     };
     auto put_sig = [&](int r, const Real *h, Real dp) {
         Real dT = h[0];
@@ -356,13 +368,14 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         s_sp[r & 3][ch + 1] = v;
     };
     // grad phi = grad (phi - phi0) + (0, d_y phi0); the normal as (n_x, n_y - 1)
-    auto put_n = [&](int r) {
+    auto put_n_g = [&](int r, Real gref) {
         Real gx, gy;
         R2 n;
         grad3_(s_phi[(r - 1) & 7], s_phi[r & 7], s_phi[(r + 1) & 7], ch + 2, gx, gy);
-        unit_normal_dev_(gx, gy + __ldg(t_gref + r), P.g2min, n.x, n.y);
+        unit_normal_dev_(gx, gy + gref, P.g2min, n.x, n.y);
         s_n[r & 3][ch + 1] = n;
     };
+    auto put_n = [&](int r) { put_n_g(r, __ldg(t_gref + r)); };
     // After a wait gave up: flag the fault, let every copy this CTA started land, return.
     // (k_fail: the stage whose wait gave up; the later ones issued are waited for once more)
     auto fail = [&](int k_fail, int k_last) {
@@ -420,16 +433,17 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     for (int y = y0; y < y1; ++y) {
         Real fq3[QF], hq1[QT], g[9];
         if (!mbar_wait_(&s_bar[sl], par)) s_abort = 1;
+        const Real *rx = stage_rx(sl);   // this row's reference values
         if (doF) {
             read_f(sl, fq3);
-            put_phi(y + 3, fq3);
+            put_phi_dr(y + 3, fq3, rx[RX_DR3], rx[RX_DR3LO]);
         }
         if (y >= 1 && y <= ny - 3) {   // rows y and y + 1 are clear of the walls
             if (doH) {
                 Real dp;
                 read_h(std::false_type(), sl, y + 1, hq1, dp);
                 put_sig(y + 1, hq1, dp);
-                put_n(y + 1);
+                put_n_g(y + 1, rx[RX_GREF1]);
             }
             if (colt) read_g(std::false_type(), sl, y, g);
         } else {
@@ -437,10 +451,12 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
                 Real dp;
                 read_h(std::true_type(), sl, y + 1, hq1, dp);
                 put_sig(y + 1, hq1, dp);
-                put_n(y + 1);
+                put_n_g(y + 1, rx[RX_GREF1]);
             }
             if (colt) read_g(std::true_type(), sl, y, g);
         }
+        // the collision's reference values, read before the slot is refilled
+        const Real phi_ref = rx[RX_PHI0], th0 = rx[RX_TH0], c01 = rx[RX_C01], gref = rx[RX_GREF];
         // refill the slot read one row ago (every thread is past its reads) with row y + D - 1
         issue(y + D - 1, sl == 0 ? D - 1 : sl - 1);
         if (++sl == D) {
@@ -455,11 +471,11 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         if (xin) {
             const int c = tid + 2, s = tid + 1;
             const Real *pm = s_phi[(y - 1) & 7], *p0 = s_phi[y & 7], *pp = s_phi[(y + 1) & 7];
-            const Real dphi = p0[c], phi_ref = __ldg(t_phi0 + y), th0 = __ldg(t_th0 + y);
+            const Real dphi = p0[c];
             const Real phi = phi_ref + dphi;
             Real gpx, gpy;
             grad3_(pm, p0, pp, c, gpx, gpy);
-            gpy += __ldg(t_gref + y);
+            gpy += gref;
             const Real g2 = gpx * gpx + gpy * gpy;
             const R2 *nm = s_n[(y - 1) & 3], *n0 = s_n[y & 3], *np = s_n[(y + 1) & 3];
             const R2 *qm = s_sp[(y - 1) & 3], *q0 = s_sp[y & 3], *qp = s_sp[(y + 1) & 3];
@@ -496,8 +512,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real om_T = rcp_(Real(3) * (P.kA + phi * P.dk) * irho + hf);
             // theta(phi) - theta(phi0) = (4 / W) dphi (1 - 2 phi0 - dphi)
             const Real dth = P.W4 * dphi * (Real(1) - Real(2) * phi_ref - dphi);
-            collide_phase_dev_<QF>(fq0, dphi, phi, ux, uy, nxv, nC.y, th0, dth, __ldg(t_c01 + y), P.Mphi,
-                                   P.omega_phi);
+            collide_phase_dev_<QF>(fq0, dphi, phi, ux, uy, nxv, nC.y, th0, dth, c01, P.Mphi, P.omega_phi);
             collide_flow_(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy);
             collide_energy_<QT>(hq0, dT, ux, uy, P.T_ref, om_T);
             const int o = y * pitch + x;
