@@ -336,7 +336,7 @@ def bench_sweep(args):
     pkg.build()
     pkg.load()
     cases = WL.sweep_cases(96, seed=0)[:args.sweep]
-    K = 100
+    K = args.sweep_k
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b = pkg.LbmBatch(cases, precision="fp32")
@@ -426,6 +426,7 @@ def main(argv=None):
     ap.add_argument("--trends", action="store_true", help="run the Sec. 6 parametric study (U_max trends)")
     ap.add_argument("--sweep-tol", type=float, default=1e-5)
     ap.add_argument("--sweep-max", type=int, default=60000)
+    ap.add_argument("--sweep-k", type=int, default=100, help="sweep: steps between residual checks (even)")
     ap.add_argument("--warmstart", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
                     help="learned warm start: train on TRAIN channels, compare on TEST channels")
     ap.add_argument("--train-iters", type=int, default=3000)

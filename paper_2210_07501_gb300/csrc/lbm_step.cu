@@ -121,15 +121,20 @@ __device__ __forceinline__ uint64_t globaltimer_()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for the completion of the phase of `bar` with the given parity.  Gives up after
-// about one second (returns false): a copy that never lands must not hang the GPU.
+// Wait for the completion of the phase of `bar` with the given parity until the
+// %globaltimer deadline t_end (ns); false if it passed: a copy that never lands must not
+// hang the GPU.
+__device__ __forceinline__ bool mbar_wait_until_(uint64_t *bar, uint32_t parity, uint64_t t_end)
+{
+    while (!mbar_try_wait_(bar, parity))
+        if (globaltimer_() > t_end) return false;
+    return true;
+}
+// the same with a limit of about one second from now
 __device__ __forceinline__ bool mbar_wait_(uint64_t *bar, uint32_t parity)
 {
     if (mbar_try_wait_(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_();
-    while (!mbar_try_wait_(bar, parity))
-        if (globaltimer_() - t0 > 1000000000ull) return false;
-    return true;
+    return mbar_wait_until_(bar, parity, globaltimer_() + 1000000000ull);
 }
 // one element: cp.async (4 or 8 bytes), or a plain load and store
 template <bool ASYNC, typename T>
@@ -376,13 +381,18 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         s_n[r & 3][ch + 1] = n;
     };
     auto put_n = [&](int r) { put_n_g(r, __ldg(t_gref + r)); };
-    // After a wait gave up: flag the fault, let every copy this CTA started land, return.
-    // (k_fail: the stage whose wait gave up; the later ones issued are waited for once more)
+    // After a wait gave up: flag the fault, let the copies this CTA started land, return.
+    // (k_fail: the stage whose wait gave up; the later stages issued are waited for once
+    // more, all within one further second.)  The path assumes that every issued copy, a
+    // read of valid global memory, completes in the end; it is exercised with the test hook
+    // that makes each stage expect more bytes than it copies.
     auto fail = [&](int k_fail, int k_last) {
         cp_wait_all_();
         if (tid == 0) {
             if (A.fault) atomicOr(A.fault, 1u);
-            for (int k = k_fail + 1; k <= k_last; ++k) mbar_wait_(&s_bar[k % D], uint32_t((k / D) & 1));
+            const uint64_t t_end = globaltimer_() + 1000000000ull;
+            for (int k = k_fail + 1; k <= k_last; ++k)
+                if (!mbar_wait_until_(&s_bar[k % D], uint32_t((k / D) & 1), t_end)) break;
         }
     };
 

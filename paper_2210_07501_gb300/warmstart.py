@@ -109,25 +109,28 @@ def plain_per_case(cases, tol, max_steps, precision="fp32", init=None, K=100, st
 
 def experiment(train_cases, test_cases, tol=1e-5, max_steps=60000, iters=2000, batch=16, lr=1e-3, seed=0,
                precision="fp32", log_every=0, plain_cases=0, extra_starts=None, train_tol=None, train_max_steps=None,
-               K=100):
+               K=100, progress=None):
     """Full pipeline; returns a dict of measurements.  Runs on one dedicated stream, shared
     by torch's tensor operations and the library's kernels.  The training channels run to
     train_tol / train_max_steps (default: tol / max_steps), the held-out ones to tol, with
     K steps between residual checks.  extra_starts: optional {name: [initial fields per
-    test case]} run as further variants."""
+    test case]} run as further variants.  progress: optional callable(name, dict) told the
+    result of each phase as soon as it is done."""
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         return _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every,
-                           stream, plain_cases, extra_starts, train_tol or tol, train_max_steps or max_steps, K)
+                           stream, plain_cases, extra_starts, train_tol or tol, train_max_steps or max_steps, K,
+                           progress or (lambda name, d: None))
 
 
 def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every, stream,
-                plain_cases, extra_starts, train_tol, train_max_steps, K):
+                plain_cases, extra_starts, train_tol, train_max_steps, K, progress):
     t0 = time.perf_counter()
     f_train, s_train, c_train, _ = steady_batch(train_cases, train_tol, train_max_steps, precision, K=K,
                                                 stream=stream)
     t_data = time.perf_counter() - t0
+    progress("training_data", {"seconds": t_data, "converged": int(c_train.sum()), "steps_mean": float(s_train.mean())})
     X, Y = dataset(train_cases, f_train)
     scale = target_scale(Y)
     H, W = X.shape[2], X.shape[3]
@@ -136,14 +139,17 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
     losses = train(net, X, Y / scale[None, :, None, None], iters=iters, batch=batch, lr=lr, seed=seed,
                    log_every=log_every)
     t_train = time.perf_counter() - t0
+    progress("training", {"seconds": t_train, "loss_first": float(losses[0]), "loss_last": float(np.mean(losses[-20:]))})
     Xt = np.stack([S.features(c["domain"], c["params"]) for c in test_cases])
     t0 = time.perf_counter()
     P = predict(net, Xt, scale)
     t_pred = time.perf_counter() - t0
     init = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True) for c, p in zip(test_cases, P)]
     f_cold, s_cold, c_cold, t_cold = steady_batch(test_cases, tol, max_steps, precision, K=K, stream=stream)
+    progress("cold", {"seconds": t_cold, "converged": int(c_cold.sum()), "steps_mean": float(s_cold.mean())})
     f_warm, s_warm, c_warm, t_warm = steady_batch(test_cases, tol, max_steps, precision, init=init, K=K,
                                                   stream=stream)
+    progress("warm", {"seconds": t_warm, "converged": int(c_warm.sum()), "steps_mean": float(s_warm.mean())})
     net.close()
     # variants: the surrogate's T alone; T, interface and velocity; the caller's starts
     variants = {}
@@ -162,6 +168,7 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
                           "fewer_steps_cases": int(np.sum(sv < s_cold)),
                           "final_vs_cold_rel_l2": {k: float(np.mean([rel_l2(fv[i][k], f_cold[i][k]) for i in bv]))
                                                    if bv.size else None for k in ("phi", "u", "v", "T")}}
+        progress(name, {k: v for k, v in variants[name].items() if k != "steps"})
     # the surrogate's own error against the converged cold-start LB fields (the reference)
     pred_fields = [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True, use_velocity=True)
                    for c, p in zip(test_cases, P)]
