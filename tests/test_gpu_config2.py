@@ -133,13 +133,15 @@ def test_steady_state_fp32_to_1e8():
     r <= 1e-8, residual checks every 1000 steps, from the closed-form temperature with the
     fluid at rest; residual history and the steady interface velocity and temperature
     against the closed form.  Default: 600,000 steps (the history and the comparison at
-    that point); LBM_STEADY_FULL=1: up to 4M steps or r <= 1e-8 (prints one JSON line)."""
+    that point); LBM_STEADY_FULL=1: up to 4M steps or r <= 1e-8 (prints one JSON line);
+    LBM_STEADY_PRECISION=fp64 runs the FP64 path instead."""
     import json
     import time
     from paper_2210_07501_gb300 import Lbm
     full = os.environ.get("LBM_STEADY_FULL") == "1"
+    precision = os.environ.get("LBM_STEADY_PRECISION", "fp32")
     w = case(2e-5)
-    g = Lbm(w["domain"], w["params"], precision="fp32")
+    g = Lbm(w["domain"], w["params"], precision=precision)
     g.lbm_set_check_interval(1000)
     g.lbm_init_fields(T=closed_form_T(w))
     g.lbm_autotune(3)
@@ -153,8 +155,8 @@ def test_steady_state_fp32_to_1e8():
     f = g.lbm_fields()
     g.close()
     cmp = against_closed_form(w, f)
-    print(json.dumps({"steady_fp32": {"converged": bool(ok), "steps": done, "seconds": secs, "history": hist,
-                                      "closed_form": cmp}}))
+    print(json.dumps({"steady": {"precision": precision, "converged": bool(ok), "steps": done, "seconds": secs,
+                                 "history": hist, "closed_form": cmp}}))
     # the residual keeps falling: by more than 5x between 100k and 600k steps (measured
     # 1.07e-6 -> 8.5e-8 with checks every 100 steps)
     assert hist[-1][1] < 0.2 * hist[0][1] or ok
