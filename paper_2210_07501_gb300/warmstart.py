@@ -109,23 +109,24 @@ def plain_per_case(cases, tol, max_steps, precision="fp32", init=None, K=100, st
 
 def experiment(train_cases, test_cases, tol=1e-5, max_steps=60000, iters=2000, batch=16, lr=1e-3, seed=0,
                precision="fp32", log_every=0, plain_cases=0, extra_starts=None, train_tol=None, train_max_steps=None,
-               K=100, progress=None):
+               K=100, progress=None, variants=True):
     """Full pipeline; returns a dict of measurements.  Runs on one dedicated stream, shared
     by torch's tensor operations and the library's kernels.  The training channels run to
     train_tol / train_max_steps (default: tol / max_steps), the held-out ones to tol, with
     K steps between residual checks.  extra_starts: optional {name: [initial fields per
-    test case]} run as further variants.  progress: optional callable(name, dict) told the
-    result of each phase as soon as it is done."""
+    test case]} run as further variants (variants=False: only those, not the surrogate's own
+    variants).  progress: optional callable(name, dict) told the result of each phase as
+    soon as it is done."""
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         return _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every,
                            stream, plain_cases, extra_starts, train_tol or tol, train_max_steps or max_steps, K,
-                           progress or (lambda name, d: None))
+                           progress or (lambda name, d: None), variants)
 
 
 def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed, precision, log_every, stream,
-                plain_cases, extra_starts, train_tol, train_max_steps, K, progress):
+                plain_cases, extra_starts, train_tol, train_max_steps, K, progress, with_variants):
     t0 = time.perf_counter()
     f_train, s_train, c_train, _ = steady_batch(train_cases, train_tol, train_max_steps, precision, K=K,
                                                 stream=stream)
@@ -157,6 +158,8 @@ def _experiment(train_cases, test_cases, tol, max_steps, iters, batch, lr, seed,
                                for c, p in zip(test_cases, P)]),
               ("surrogate_T_phi_u_v", [S.fields_from_prediction(c["domain"], c["params"], p, use_phi=True,
                                                                 use_velocity=True) for c, p in zip(test_cases, P)])]
+    if not with_variants:
+        starts = []
     starts += list((extra_starts or {}).items())
     for name, ini in starts:
         fv, sv, cv, tv = steady_batch(test_cases, tol, max_steps, precision, init=ini, K=K, stream=stream)

@@ -7,7 +7,11 @@ heating profile and the geometry.
 Default: a small case (64 x 32 channels, 96 training seeds run to r <= 1e-6, 8 held-out
 seeds run to r <= 1e-7).  The full experiment (256 x 64, 2000 training seeds to r <= 1e-6,
 200 held-out seeds to r <= 1e-8 with residual checks every 1000 steps) runs with
-LBM_WARMSTART_FULL=1; it prints one JSON line with every measurement."""
+LBM_WARMSTART_FULL=1; it prints one JSON line with every measurement.  In that mode
+LBM_WARMSTART_TRAIN / _TEST set the seed counts, _TRAIN_TOL / _TRAIN_MAX how far the
+training channels are run, _TOL the held-out tolerance, _PLAIN how many held-out channels
+are also timed one by one, and LBM_WARMSTART_VARIANTS=0 drops the surrogate's partial
+starts (temperature alone; temperature, interface and velocity)."""
 import json
 import os
 
@@ -38,9 +42,11 @@ def run(full: bool):
     if full:
         train = WL.surrogate_cases(int(os.environ.get("LBM_WARMSTART_TRAIN", "2000")), seed=1000)
         test = WL.surrogate_cases(int(os.environ.get("LBM_WARMSTART_TEST", "200")), seed=2000)
-        kw = dict(tol=float(os.environ.get("LBM_WARMSTART_TOL", "1e-8")), max_steps=3000000, K=1000,
-                  train_tol=1e-6, train_max_steps=400000, iters=3000, batch=16, lr=1e-3,
-                  plain_cases=int(os.environ.get("LBM_WARMSTART_PLAIN", "0")))
+        env = os.environ.get
+        kw = dict(tol=float(env("LBM_WARMSTART_TOL", "1e-8")), max_steps=3000000, K=1000,
+                  train_tol=float(env("LBM_WARMSTART_TRAIN_TOL", "1e-6")),
+                  train_max_steps=int(env("LBM_WARMSTART_TRAIN_MAX", "400000")), iters=3000, batch=16, lr=1e-3,
+                  plain_cases=int(env("LBM_WARMSTART_PLAIN", "0")), variants=env("LBM_WARMSTART_VARIANTS", "1") == "1")
     else:
         train = WL.surrogate_cases(96, seed=11, nx=64, ny=32)
         test = WL.surrogate_cases(8, seed=12, nx=64, ny=32)
@@ -57,10 +63,10 @@ def test_warm_start_against_cold_and_closed_form():
     r = run(full)
     print(json.dumps(r))
     cf = r["variants"]["closed_form_T"]
+    v = r["variants"]
     print(f"mean steps to r <= {r['tol']:g}: cold {r['cold_steps_mean']:.0f}, closed-form T "
-          f"{cf['steps_mean']:.0f}, surrogate T {r['variants']['surrogate_T']['steps_mean']:.0f}, "
-          f"surrogate T + phi {r['warm_steps_mean']:.0f}, surrogate T + phi + u, v "
-          f"{r['variants']['surrogate_T_phi_u_v']['steps_mean']:.0f}")
+          f"{cf['steps_mean']:.0f}, surrogate T + phi {r['warm_steps_mean']:.0f}" +
+          "".join(f", {k} {v[k]['steps_mean']:.0f}" for k in ("surrogate_T", "surrogate_T_phi_u_v") if k in v))
     if full:
         # 256 x 64 to r <= 1e-8: the settling of the interface, which the conservative phase
         # field does by redistributing phi along the channel (a time of order L^2 / M_phi ~
