@@ -273,19 +273,18 @@ __device__ __forceinline__ void raw_first_(const Real *p, Real &m10, Real &m01)
 
 // ---- Sec. 4.1 phase-field collision in deviation variables.  The first central moments
 // relax at omega_phi towards M_phi theta n, the rest take their equilibria (phi, c^2 phi,
-// c^2 phi, 0, 0, 0, c^4 phi).  In: s = pulled f - r (r the reference populations at the
-// rows they were pulled from), dphi = phi - phi0(y), phi, u, the normal (n_x, n_y - 1),
-// theta0 = theta(phi0(y)) and dth = theta(phi) - theta0, c01 (see StepArgs::rtab).  Out:
-// s = post-collision f - r(y).  With Rx = sum e_x r(pulled) = 0 (the reference is even
-// in x) the pre-collision first central moments are k10 = sum e_x s - u_x phi and
-// k01 = sum e_y s + Ry(y) - u_y phi; the reference's own post-collision first moments are
+// c^2 phi, 0, 0, 0, c^4 phi), so of the pre-collision populations only phi and the first
+// raw moments enter.  In: (m10, m01) = raw_first_ of the pulled f - r (r the reference
+// populations at the rows they were pulled from), dphi = phi - phi0(y), phi, u, the normal
+// (n_x, n_y - 1), theta0 = theta(phi0(y)) and dth = theta(phi) - theta0, c01 (see
+// StepArgs::rtab).  Out: s = post-collision f - r(y).  With Rx = sum e_x r(pulled) = 0 (the
+// reference is even in x) the pre-collision first central moments are k10 = m10 - u_x phi
+// and k01 = m01 + Ry(y) - u_y phi; the reference's own post-collision first moments are
 // (0, t01(y)), t01 ~ M_phi theta0. ----
 template <int Q, typename Real>
-__device__ __forceinline__ void collide_phase_dev_(Real *s, Real dphi, Real phi, Real ux, Real uy, Real nx, Real my,
-                                                   Real th0, Real dth, Real c01, Real M, Real om)
+__device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, Real dphi, Real phi, Real ux, Real uy,
+                                                   Real nx, Real my, Real th0, Real dth, Real c01, Real M, Real om)
 {
-    Real m10, m01;
-    raw_first_<Q>(s, m10, m01);
     const Real w1 = Real(1) - om, oM = om * M;
     const Real t10 = w1 * (m10 - ux * phi) + oM * (th0 + dth) * nx;
     const Real dt01 = w1 * (m01 - uy * phi) + oM * (th0 * my + dth * (Real(1) + my)) + c01;
@@ -304,12 +303,12 @@ __device__ __forceinline__ void collide_phase_dev_(Real *s, Real dphi, Real phi,
 
 // ---- Sec. 4.3 energy collision on h - w T_ref: first central moments relax at omega_T;
 // the rest take (T E - T_ref Wc(u)) = dT E + T_ref D(u), where E = (1,0,0,c^2,c^2,0,0,0,c^4)
-// are the Maxwellian central moments per unit T and Wc(u) those of the weights. ----
+// are the Maxwellian central moments per unit T and Wc(u) those of the weights.  In: the
+// pulled populations' dT = T - T_ref and first raw moments (m10, m01); out: h = the
+// post-collision populations. ----
 template <int Q, typename Real>
-__device__ __forceinline__ void collide_energy_(Real *h, Real dT, Real ux, Real uy, Real Tr, Real om)
+__device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Real dT, Real ux, Real uy, Real Tr, Real om)
 {
-    Real m10, m01;
-    raw_first_<Q>(h, m10, m01);
     const Real k10 = m10 - ux * dT, k01 = m01 - uy * dT;
     const Real t10 = k10 + om * (Tr * ux - k10), t01 = k01 + om * (Tr * uy - k01);
     const Real c2 = Real(1.0 / 3.0);

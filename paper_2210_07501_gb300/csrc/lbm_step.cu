@@ -22,8 +22,9 @@ namespace lbm {
 // memory holds rings of the last rows: phi - phi0 (8 rows, radius-2 halo columns), the
 // pair (sigma - sigma0, p - p0) and the unit normal as (n_x, n_y - 1) (4 rows, radius-1
 // halo columns).  For output
-// row y the CTA adds phi of row y + 3 (from f pulled there, kept in registers until row y
-// collides), sigma and p of row y + 1 (from h pulled there, kept one row), the normals of
+// row y the CTA adds phi of row y + 3 (from f pulled there, whose first raw moments stay
+// in registers until row y collides: the collision needs no more of them), sigma and p of
+// row y + 1 (from h pulled there; T and the first raw moments kept one row), the normals of
 // row y + 1, and then collides row y.  The population rows come from a ring of D stages
 // in shared memory filled by bulk copies D - 1 rows ahead (below); the first rows of a
 // segment are loaded directly.  Every thread works on the same row, so wall tests and row
@@ -165,15 +166,16 @@ __device__ __forceinline__ Real lds_(const Store *p)
     else return Real(*p);
 }
 
-#ifndef LBM_FP32_TX
-#define LBM_FP32_TX 128
-#endif
-// Columns per strip: 128 (FP32 and FP16 storage: four CTAs of 5 warps per SM; 256 runs 2 %
-// slower on the 8192 x 2048 channel); FP64 needs ~150-220 registers per thread, so 128 with
-// two CTAs per SM.
-template <typename Real> constexpr int march_width() { return std::is_same<Real, double>::value ? 128 : LBM_FP32_TX; }
+// Columns per strip: 128.  FP32 and FP16 storage: five CTAs of 5 warps per SM (72 registers
+// per thread, a three-stage ring for FP32; measured 1 % faster than four CTAs with a
+// four-stage ring on the 8192 x 2048 channel, 11 % for FP16; 256 columns ran 2 % slower).
+// FP64 needs ~125-165 registers per thread: two CTAs per SM.
+template <typename Real> constexpr int march_width() { return 128; }
 // Resident CTAs per SM the kernels are built for (registers and shared memory).
-template <typename Real> constexpr int march_ctas() { return march_width<Real>() == 128 && sizeof(Real) == 4 ? 4 : 2; }
+template <typename Real> constexpr int march_ctas() { return sizeof(Real) == 4 ? 5 : 2; }
+// The many-channel kernel reads its arguments through a pointer and needs more registers:
+// at 72 it spilled and ran the 16-channel sweep 14 % slower than with four CTAs per SM.
+template <typename Real> constexpr int batch_ctas() { return sizeof(Real) == 4 ? 4 : 2; }
 
 // Shared-memory geometry of the staging ring (host and device).
 template <typename Real, typename Store, int QF, int QT, int TX> struct StageGeo {
@@ -182,7 +184,7 @@ template <typename Real, typename Store, int QF, int QT, int TX> struct StageGeo
     static constexpr int RS = TX + 2 * HS, RD = TX + 2 * HD; // staged row lengths (16-byte multiples)
     static constexpr int NP = QF + QT + 9;                   // population planes per stage: f, h, g
     static constexpr int RXO = NP * RS * (int)sizeof(Store) + RD * (int)sizeof(Real);   // reference values
-    static constexpr int BYTES = (RXO + RX_N * (int)sizeof(Real) + 127) / 128 * 128;
+    static constexpr int BYTES = (RXO + RX_N * (int)sizeof(Real) + 15) / 16 * 16;   // bulk copies need 16 B
     static_assert(RXO % 16 == 0, "the staged reference values need a 16-byte aligned slot");
     static constexpr int RINGS = 8 * (TX + 4) * (int)sizeof(Real) + 16 * (TX + 2) * (int)sizeof(Real);
     // deepest ring that leaves room for march_ctas() CTAs per SM (228 KiB, 1 KiB reserved per CTA)
@@ -361,16 +363,26 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         const int gy = mirror_row_(r, ny);
         put_phi_dr(r, f, __ldg(t_dR + gy), __ldg(t_dRlo + gy));
     };
-    auto put_sig = [&](int r, const Real *h, Real dp) {
+    // returns T - T_ref of the pulled populations (of row r itself, not the ghost value)
+    auto put_sig = [&](int r, const Real *h, Real dp) -> Real {
         Real dT = h[0];
 #pragma unroll
         for (int a = 1; a < QT; ++a) dT += h[a];
-        if (r == -1) dT = Real(2) * A.twall[nx + xh] - dT;   // T_ghost = 2 T_w - T_adjacent
-        else if (r == ny) dT = Real(2) * P.dTcold - dT;
+        Real dTs = dT;
+        if (r == -1) dTs = Real(2) * A.twall[nx + xh] - dT;   // T_ghost = 2 T_w - T_adjacent
+        else if (r == ny) dTs = Real(2) * P.dTcold - dT;
         R2 v;
-        v.x = dT * (P.sigma1 + P.sigma2 * dT);
+        v.x = dTs * (P.sigma1 + P.sigma2 * dTs);
         v.y = dp;
         s_sp[r & 3][ch + 1] = v;
+        return dT;
+    };
+    // what the collisions keep of pulled populations: first raw moments of f, and
+    // (T - T_ref, first raw moments) of h
+    auto keep_f = [&](const Real *f, Real *m) { raw_first_<QF>(f, m[0], m[1]); };
+    auto keep_h = [&](const Real *h, Real dT, Real *m) {
+        m[0] = dT;
+        raw_first_<QT>(h, m[1], m[2]);
     };
     // grad phi = grad (phi - phi0) + (0, d_y phi0); the normal as (n_x, n_y - 1)
     auto put_n_g = [&](int r, Real gref) {
@@ -406,26 +418,31 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < D - 1; ++k) issue(y0 + k, k);
-    Real fq0[QF], fq1[QF], fq2[QF], hq0[QT];
+    // first raw moments of f pulled at rows y0 .. y0 + 2 and (T - T_ref, first raw
+    // moments) of h pulled at row y0: all the collisions need of those populations
+    Real fm0[2], fm1[2], fm2[2], hm0[3];
     if (doF) {
         Real t[QF];
         load_f(y0 - 2, t);
         put_phi(y0 - 2, t);
         load_f(y0 - 1, t);
         put_phi(y0 - 1, t);
-        load_f(y0, fq0);
-        put_phi(y0, fq0);
-        load_f(y0 + 1, fq1);
-        put_phi(y0 + 1, fq1);
-        load_f(y0 + 2, fq2);
-        put_phi(y0 + 2, fq2);
+        load_f(y0, t);
+        put_phi(y0, t);
+        keep_f(t, fm0);
+        load_f(y0 + 1, t);
+        put_phi(y0 + 1, t);
+        keep_f(t, fm1);
+        load_f(y0 + 2, t);
+        put_phi(y0 + 2, t);
+        keep_f(t, fm2);
     }
     if (doH) {
         Real t[QT], dp;
         load_h(y0 - 1, t, dp);
         put_sig(y0 - 1, t, dp);
-        load_h(y0, hq0, dp);
-        put_sig(y0, hq0, dp);
+        load_h(y0, t, dp);
+        keep_h(t, put_sig(y0, t, dp), hm0);
     }
     __syncthreads();
     if (doH) {
@@ -441,26 +458,28 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     // after it, row y collides.  The rings are deep enough that these writes never touch
     // rows the previous row's collision may still be reading.
     for (int y = y0; y < y1; ++y) {
-        Real fq3[QF], hq1[QT], g[9];
+        Real fm3[2], hm1[3], g[9];
         if (!mbar_wait_(&s_bar[sl], par)) s_abort = 1;
         const Real *rx = stage_rx(sl);   // this row's reference values
         if (doF) {
-            read_f(sl, fq3);
-            put_phi_dr(y + 3, fq3, rx[RX_DR3], rx[RX_DR3LO]);
+            Real t[QF];
+            read_f(sl, t);
+            put_phi_dr(y + 3, t, rx[RX_DR3], rx[RX_DR3LO]);
+            keep_f(t, fm3);
         }
         if (y >= 1 && y <= ny - 3) {   // rows y and y + 1 are clear of the walls
             if (doH) {
-                Real dp;
-                read_h(std::false_type(), sl, y + 1, hq1, dp);
-                put_sig(y + 1, hq1, dp);
+                Real t[QT], dp;
+                read_h(std::false_type(), sl, y + 1, t, dp);
+                keep_h(t, put_sig(y + 1, t, dp), hm1);
                 put_n_g(y + 1, rx[RX_GREF1]);
             }
             if (colt) read_g(std::false_type(), sl, y, g);
         } else {
             if (doH) {
-                Real dp;
-                read_h(std::true_type(), sl, y + 1, hq1, dp);
-                put_sig(y + 1, hq1, dp);
+                Real t[QT], dp;
+                read_h(std::true_type(), sl, y + 1, t, dp);
+                keep_h(t, put_sig(y + 1, t, dp), hm1);
                 put_n_g(y + 1, rx[RX_GREF1]);
             }
             if (colt) read_g(std::true_type(), sl, y, g);
@@ -501,9 +520,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real dpx = c1 * (qE.y - qW.y) + cd * ((qNE.y - qNW.y) + (qSE.y - qSW.y));
             const Real dpy = c1 * (qN.y - qS.y) + cd * ((qNE.y - qSE.y) + (qNW.y - qSW.y));
             const Real nxv = nC.x, nyv = Real(1) + nC.y;
-            Real dT = hq0[0];
-#pragma unroll
-            for (int a = 1; a < QT; ++a) dT += hq0[a];
+            const Real dT = hm0[0];
             const Real sigma = P.sigma0 + dT * (P.sigma1 + P.sigma2 * dT);
             const Real Fsx = P.csf * (-sigma * g2 * divn * nxv + g2 * ((Real(1) - nxv * nxv) * dsx - nxv * nyv * dsy));
             const Real Fsy = P.csf * (-sigma * g2 * divn * nyv + g2 * ((Real(1) - nyv * nyv) * dsy - nxv * nyv * dsx));
@@ -522,9 +539,11 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real om_T = rcp_(Real(3) * (P.kA + phi * P.dk) * irho + hf);
             // theta(phi) - theta(phi0) = (4 / W) dphi (1 - 2 phi0 - dphi)
             const Real dth = P.W4 * dphi * (Real(1) - Real(2) * phi_ref - dphi);
-            collide_phase_dev_<QF>(fq0, dphi, phi, ux, uy, nxv, nC.y, th0, dth, c01, P.Mphi, P.omega_phi);
+            Real fo[QF], ho[QT];
+            collide_phase_dev_<QF>(fo, fm0[0], fm0[1], dphi, phi, ux, uy, nxv, nC.y, th0, dth, c01, P.Mphi,
+                                   P.omega_phi);
             collide_flow_(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy);
-            collide_energy_<QT>(hq0, dT, ux, uy, P.T_ref, om_T);
+            collide_energy_<QT>(ho, hm0[1], hm0[2], dT, ux, uy, P.T_ref, om_T);
             const int o = y * pitch + x;
             // one unsigned 32-bit byte offset from every plane's base (measured 2 % faster than
             // plane base + element index)
@@ -532,7 +551,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             auto at = [&](Store *base) { return reinterpret_cast<Store *>(reinterpret_cast<char *>(base) + ob); };
 #pragma unroll
             for (int a = 0; a < QF; ++a) {
-                Real v = fq0[a];
+                Real v = fo[a];
                 if constexpr (scaled_<Store>()) v *= A.sf;
                 st_(at(A.fo[a]), v);
             }
@@ -544,7 +563,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             }
 #pragma unroll
             for (int a = 0; a < QT; ++a) {
-                Real v = hq0[a];
+                Real v = ho[a];
                 if constexpr (scaled_<Store>()) v *= A.sh;
                 st_(at(A.ho[a]), v);
             }
@@ -559,13 +578,13 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             }
         }
 #pragma unroll
-        for (int a = 0; a < QF; ++a) {
-            fq0[a] = fq1[a];
-            fq1[a] = fq2[a];
-            fq2[a] = fq3[a];
+        for (int a = 0; a < 2; ++a) {
+            fm0[a] = fm1[a];
+            fm1[a] = fm2[a];
+            fm2[a] = fm3[a];
         }
 #pragma unroll
-        for (int a = 0; a < QT; ++a) hq0[a] = hq1[a];
+        for (int a = 0; a < 3; ++a) hm0[a] = hm1[a];
     }
 }
 
@@ -579,7 +598,7 @@ __global__ void __launch_bounds__(TX + 32, march_ctas<Real>()) march_kernel(cons
 // ctas[i].z of case ctas[i].x, with that case's arguments; cases whose active flag is 0
 // (converged) are skipped.
 template <typename Real, typename Store, int QF, int QT, int TX>
-__global__ void __launch_bounds__(TX + 32, march_ctas<Real>()) batch_kernel(const StepArgs<Real, Store> *__restrict__ cases,
+__global__ void __launch_bounds__(TX + 32, batch_ctas<Real>()) batch_kernel(const StepArgs<Real, Store> *__restrict__ cases,
                                                        const int4 *__restrict__ ctas, const int *__restrict__ active,
                                                        int seg)
 {
