@@ -202,6 +202,75 @@ __device__ __forceinline__ void unit_normal_dev_(Real gx, Real gy, Real g2min, R
     }
 }
 
+// ---- FP32 forms with the x and y halves paired: one packed instruction (sm_100 and
+// later) does both halves of an operation.  Same terms as the generic forms below, partly
+// summed in another order; used for FP32 arithmetic only (FP64 keeps the generic forms). ----
+__device__ __forceinline__ float2 f2_(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc2_(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2_(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2_(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// D2Q9 central moments -> populations (see central_to_pop9_), FP32
+template <bool REST_LAST>
+__device__ __forceinline__ void central_to_pop9_f_(const float dk[9], const float k[9], float ux, float uy, float g[9])
+{
+    const float2 U = f2_(ux, uy), U2 = mul2_(U, U);
+    const float ux2 = U2.x, uy2 = U2.y, uxy = ux * uy;
+    const float r00 = dk[0];
+    const float2 R1 = fma2_(U, bc2_(k[0]), f2_(dk[1], dk[2]));                                         // r10, r01
+    const float2 R2 = fma2_(U2, bc2_(k[0]), fma2_(add2_(U, U), f2_(k[1], k[2]), f2_(dk[3], dk[4])));   // r20, r02
+    const float r11 = dk[5] + uy * k[1] + ux * k[2] + uxy * k[0];
+    const float r21 = dk[6] + 2.f * ux * k[5] + uy * k[3] + ux2 * k[2] + 2.f * uxy * k[1] + ux2 * uy * k[0];
+    const float r12 = dk[7] + 2.f * uy * k[5] + ux * k[4] + uy2 * k[1] + 2.f * uxy * k[2] + ux * uy2 * k[0];
+    const float r22 = dk[8] + 2.f * ux * k[7] + 2.f * uy * k[6] + ux2 * k[4] + uy2 * k[3] + 4.f * uxy * k[5] +
+                      2.f * uxy * uy * k[1] + 2.f * uxy * ux * k[2] + ux2 * uy2 * k[0];
+    const float2 Q = f2_(r12, r21), W = f2_(r11, r22);
+    const float2 E = sub2_(R2, bc2_(r22));   // r20 - r22, r02 - r22
+    const float2 V = sub2_(R1, Q);            // r10 - r12, r01 - r21
+    const float2 G12 = mul2_(bc2_(0.5f), add2_(E, V));   // g1, g2
+    const float2 G34 = mul2_(bc2_(0.5f), sub2_(E, V));   // g3, g4
+    const float2 S = add2_(W, Q);                         // r11 + r12, r22 + r21
+    const float2 D = sub2_(W, Q);                         // r11 - r12, r22 - r21
+    g[1] = G12.x;
+    g[2] = G12.y;
+    g[3] = G34.x;
+    g[4] = G34.y;
+    g[5] = 0.25f * (S.x + S.y);
+    g[6] = 0.25f * (S.y - S.x);
+    g[7] = 0.25f * (D.x + D.y);
+    g[8] = 0.25f * (D.y - D.x);
+    if constexpr (REST_LAST) {
+        const float2 P = add2_(G12, G34);
+        g[0] = r00 - ((P.x + P.y) + ((g[5] + g[6]) + (g[7] + g[8])));
+    } else {
+        g[0] = r00 - R2.x - R2.y + r22;
+    }
+}
+
+// D2Q5 central moments -> populations (see central_to_pop5_), FP32: dk = (dk0, DK1, DK2),
+// k = (k0, K1, .) as pairs (first and second moments), U = (ux, uy), U2 = (ux^2, uy^2)
+template <bool REST_LAST>
+__device__ __forceinline__ void central_to_pop5_f_(float dk0, float2 DK1, float2 DK2, float k0, float2 K1, float2 U,
+                                                   float2 U2, float f[5])
+{
+    const float2 R1 = fma2_(U, bc2_(k0), DK1);                            // r10, r01
+    const float2 R2 = fma2_(U2, bc2_(k0), fma2_(add2_(U, U), K1, DK2));   // r20, r02
+    const float2 A = mul2_(bc2_(0.5f), add2_(R1, R2));                    // f1, f2
+    const float2 B = mul2_(bc2_(0.5f), sub2_(R2, R1));                    // f3, f4
+    f[1] = A.x;
+    f[2] = A.y;
+    f[3] = B.x;
+    f[4] = B.y;
+    if constexpr (REST_LAST) {
+        const float2 S = add2_(A, B);
+        f[0] = dk0 - (S.x + S.y);
+    } else {
+        f[0] = dk0 - R2.x - R2.y;
+    }
+}
+
 // ---- App. B: central moments -> populations, F(-u) then P^-1 (D2Q9).
 // Moment order 00, 10, 01, 20, 02, 11, 21, 12, 22. ----
 // dk: the central moments minus those of a reference at u = 0 (whose raw moments they
@@ -216,6 +285,10 @@ __device__ __forceinline__ void unit_normal_dev_(Real gx, Real gy, Real g2min, R
 template <typename Real, bool REST_LAST = false>
 __device__ __forceinline__ void central_to_pop9_(const Real dk[9], const Real k[9], Real ux, Real uy, Real g[9])
 {
+    if constexpr (std::is_same<Real, float>::value) {
+        central_to_pop9_f_<REST_LAST>(dk, k, ux, uy, g);
+        return;
+    }
     const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     const Real r00 = dk[0];
     const Real r10 = dk[1] + ux * k[0];
@@ -246,6 +319,12 @@ __device__ __forceinline__ void central_to_pop9_(const Real dk[9], const Real k[
 template <typename Real, bool REST_LAST = false>
 __device__ __forceinline__ void central_to_pop5_(const Real dk[5], const Real k[5], Real ux, Real uy, Real f[5])
 {
+    if constexpr (std::is_same<Real, float>::value) {
+        const float2 U = f2_(ux, uy);
+        central_to_pop5_f_<REST_LAST>(dk[0], f2_(dk[1], dk[2]), f2_(dk[3], dk[4]), k[0], f2_(k[1], k[2]), U,
+                                      mul2_(U, U), f);
+        return;
+    }
     const Real r00 = dk[0];
     const Real r10 = dk[1] + ux * k[0];
     const Real r01 = dk[2] + uy * k[0];
@@ -285,6 +364,16 @@ template <int Q, typename Real>
 __device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, Real dphi, Real phi, Real ux, Real uy,
                                                    Real nx, Real my, Real th0, Real dth, Real c01, Real M, Real om)
 {
+    if constexpr (std::is_same<Real, float>::value && Q == 5) {
+        const float w1 = 1.f - om, oM = om * M, c2 = 1.f / 3.f;
+        const float2 U = f2_(ux, uy), NU = mul2_(bc2_(-1.f), U);
+        // (t10, t01 - M theta0), then (t10, t01)
+        const float2 T = fma2_(bc2_(w1), fma2_(NU, bc2_(phi), f2_(m10, m01)),
+                               f2_(oM * (th0 + dth) * nx, oM * (th0 * my + dth * (1.f + my)) + c01));
+        const float2 T1 = add2_(T, f2_(0.f, M * th0));
+        central_to_pop5_f_<true>(dphi, T, bc2_(c2 * dphi), phi, T1, U, mul2_(U, U), s);
+        return;
+    }
     const Real w1 = Real(1) - om, oM = om * M;
     const Real t10 = w1 * (m10 - ux * phi) + oM * (th0 + dth) * nx;
     const Real dt01 = w1 * (m01 - uy * phi) + oM * (th0 * my + dth * (Real(1) + my)) + c01;
@@ -309,6 +398,15 @@ __device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, 
 template <int Q, typename Real>
 __device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Real dT, Real ux, Real uy, Real Tr, Real om)
 {
+    if constexpr (std::is_same<Real, float>::value && Q == 5) {
+        const float c2 = 1.f / 3.f;
+        const float2 U = f2_(ux, uy), U2 = mul2_(U, U);
+        const float2 K = fma2_(mul2_(bc2_(-1.f), U), bc2_(dT), f2_(m10, m01));          // k10, k01
+        const float2 T = fma2_(bc2_(om), sub2_(mul2_(bc2_(Tr), U), K), K);               // t10, t01
+        const float2 K2 = fma2_(bc2_(-Tr), U2, bc2_(c2 * dT));                           // k20, k02
+        central_to_pop5_f_<true>(dT, T, K2, dT, T, U, U2, h);
+        return;
+    }
     const Real k10 = m10 - ux * dT, k01 = m01 - uy * dT;
     const Real t10 = k10 + om * (Tr * ux - k10), t01 = k01 + om * (Tr * uy - k01);
     const Real c2 = Real(1.0 / 3.0);
@@ -338,6 +436,44 @@ template <typename Real>
 __device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real ux, Real uy, Real Fpx, Real Fpy,
                                               Real Ftx, Real Fty, Real om, Real s0, Real sx, Real sy)
 {
+    if constexpr (std::is_same<Real, float>::value) {
+        const float c2 = 1.f / 3.f, hf = 0.5f;
+        const float2 U = f2_(ux, uy), U2 = mul2_(U, U), NU = mul2_(bc2_(-1.f), U);
+        const float uxy = ux * uy;
+        const float t5678 = (g[5] + g[6]) + (g[7] + g[8]);
+        const float2 R2 = add2_(add2_(f2_(g[1], g[2]), f2_(g[3], g[4])), bc2_(t5678));          // r20, r02
+        const float r11 = (g[5] - g[6]) + (g[7] - g[8]);
+        const float2 E = fma2_(U2, bc2_(s0), fma2_(add2_(NU, NU), f2_(sx, sy), R2));          // e20, e02
+        const float e11 = r11 - uy * sx - ux * sy + uxy * s0;
+        const float2 A = add2_(bc2_(c2), U2);                                                  // ax, ay
+        const float rc2 = rho * c2, d = rc2 - dp;
+        const float2 Q1 = mul2_(U, bc2_(d));                                                   // q10, q01
+        const float2 Q2 = fma2_(bc2_(dp), A, mul2_(bc2_(-rc2), U2));                           // q20, q02
+        const float q11 = -uxy * d;
+        const float q21 = A.x * uy * d, q12 = A.y * ux * d;
+        const float q22 = dp * A.x * A.y - rc2 * (c2 * (U2.x + U2.y) + U2.x * U2.y);
+        const float G = Fpx * ux + Fpy * uy;
+        const float2 S1 = fma2_(NU, bc2_(G), mul2_(bc2_(c2), f2_(Ftx, Fty)));                  // s10, s01
+        const float2 S2 = fma2_(A, bc2_(G), mul2_(bc2_(2.f * c2), mul2_(f2_(Fpx, Fpy), U)));  // s20, s02
+        const float s11 = c2 * (Fpx * uy + Fpy * ux) + uxy * G;
+        const float sw = 1.f - hf * om;
+        const float t2s = (Q2.x + Q2.y) + hf * (S2.x + S2.y);
+        const float e2d = E.x - E.y;
+        const float t2d = e2d + om * ((Q2.x - Q2.y) - e2d) + sw * (S2.x - S2.y);
+        const float2 K1 = fma2_(bc2_(hf), S1, Q1);                                             // k10, k01
+        float k[9];
+        k[0] = dp + hf * G;
+        k[1] = K1.x;
+        k[2] = K1.y;
+        k[3] = hf * (t2s + t2d);
+        k[4] = hf * (t2s - t2d);
+        k[5] = e11 + om * (q11 - e11) + sw * s11;
+        k[6] = q21;
+        k[7] = q12;
+        k[8] = q22;
+        central_to_pop9_f_<false>(k, k, ux, uy, g);
+        return;
+    }
     const Real c2 = Real(1.0 / 3.0), hf = Real(0.5);
     const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     // pre-collision central moments 20, 02, 11 (F(u) rows on the raw moments)

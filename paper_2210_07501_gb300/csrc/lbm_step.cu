@@ -33,6 +33,24 @@ template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
 
+// The RX_N reference values of a staged row (16-byte aligned) in registers: two or four
+// 16-byte loads instead of one load per value.
+template <typename Real>
+__device__ __forceinline__ void load_rowref_(const Real *rx, Real *v)
+{
+    if constexpr (std::is_same<Real, float>::value) {
+        const float4 a = reinterpret_cast<const float4 *>(rx)[0], b = reinterpret_cast<const float4 *>(rx)[1];
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < RX_N / 2; ++i) {
+            const double2 d = reinterpret_cast<const double2 *>(rx)[i];
+            v[2 * i] = d.x, v[2 * i + 1] = d.y;
+        }
+    }
+}
+static_assert(RX_N == 8, "load_rowref_ reads eight values");
+
 template <typename Real>
 __device__ __forceinline__ void grad3_(const Real *rm, const Real *r0, const Real *rp, int c, Real &gx, Real &gy)
 {
@@ -460,7 +478,8 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     for (int y = y0; y < y1; ++y) {
         Real fm3[2], hm1[3], g[9];
         if (!mbar_wait_(&s_bar[sl], par)) s_abort = 1;
-        const Real *rx = stage_rx(sl);   // this row's reference values
+        Real rx[RX_N];   // this row's reference values, read before the slot is refilled
+        load_rowref_(stage_rx(sl), rx);
         if (doF) {
             Real t[QF];
             read_f(sl, t);
@@ -484,7 +503,6 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             }
             if (colt) read_g(std::true_type(), sl, y, g);
         }
-        // the collision's reference values, read before the slot is refilled
         const Real phi_ref = rx[RX_PHI0], th0 = rx[RX_TH0], c01 = rx[RX_C01], gref = rx[RX_GREF];
         // refill the slot read one row ago (every thread is past its reads) with row y + D - 1
         issue(y + D - 1, sl == 0 ? D - 1 : sl - 1);
@@ -511,14 +529,25 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const R2 nC = n0[s], nE = n0[s + 1], nW = n0[s - 1], nN = np[s], nS = nm[s];
             const R2 nNE = np[s + 1], nNW = np[s - 1], nSE = nm[s + 1], nSW = nm[s - 1];
             const Real c1 = Real(1.0 / 3.0), cd = Real(1.0 / 12.0);
-            const Real divn = c1 * (nE.x - nW.x) + cd * ((nNE.x - nNW.x) + (nSE.x - nSW.x)) + c1 * (nN.y - nS.y) +
-                              cd * ((nNE.y - nSE.y) + (nNW.y - nSW.y));
             const R2 qE = q0[s + 1], qW = q0[s - 1], qN = qp[s], qS = qm[s];
             const R2 qNE = qp[s + 1], qNW = qp[s - 1], qSE = qm[s + 1], qSW = qm[s - 1];
-            const Real dsx = c1 * (qE.x - qW.x) + cd * ((qNE.x - qNW.x) + (qSE.x - qSW.x));
-            const Real dsy = c1 * (qN.x - qS.x) + cd * ((qNE.x - qSE.x) + (qNW.x - qSW.x));
-            const Real dpx = c1 * (qE.y - qW.y) + cd * ((qNE.y - qNW.y) + (qSE.y - qSW.y));
-            const Real dpy = c1 * (qN.y - qS.y) + cd * ((qNE.y - qSE.y) + (qNW.y - qSW.y));
+            Real divn, dsx, dsy, dpx, dpy;
+            if constexpr (std::is_same<Real, float>::value) {
+                // the same stencils with the (n_x, n_y) and (sigma, p) halves paired; the
+                // diagonal terms of div n summed as (NE - SW) +- (SE - NW)
+                const float2 T1 = sub2_(nNE, nSW), T2 = sub2_(nSE, nNW);
+                divn = c1 * ((nE.x - nW.x) + (nN.y - nS.y)) + cd * ((T1.x + T2.x) + (T1.y - T2.y));
+                const float2 X = fma2_(bc2_(c1), sub2_(qE, qW), mul2_(bc2_(cd), add2_(sub2_(qNE, qNW), sub2_(qSE, qSW))));
+                const float2 Y = fma2_(bc2_(c1), sub2_(qN, qS), mul2_(bc2_(cd), add2_(sub2_(qNE, qSE), sub2_(qNW, qSW))));
+                dsx = X.x, dpx = X.y, dsy = Y.x, dpy = Y.y;
+            } else {
+                divn = c1 * (nE.x - nW.x) + cd * ((nNE.x - nNW.x) + (nSE.x - nSW.x)) + c1 * (nN.y - nS.y) +
+                       cd * ((nNE.y - nSE.y) + (nNW.y - nSW.y));
+                dsx = c1 * (qE.x - qW.x) + cd * ((qNE.x - qNW.x) + (qSE.x - qSW.x));
+                dsy = c1 * (qN.x - qS.x) + cd * ((qNE.x - qSE.x) + (qNW.x - qSW.x));
+                dpx = c1 * (qE.y - qW.y) + cd * ((qNE.y - qNW.y) + (qSE.y - qSW.y));
+                dpy = c1 * (qN.y - qS.y) + cd * ((qNE.y - qSE.y) + (qNW.y - qSW.y));
+            }
             const Real nxv = nC.x, nyv = Real(1) + nC.y;
             const Real dT = hm0[0];
             const Real sigma = P.sigma0 + dT * (P.sigma1 + P.sigma2 * dT);
