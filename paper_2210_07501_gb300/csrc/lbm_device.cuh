@@ -212,10 +212,13 @@ __device__ __forceinline__ float2 sub2_(float2 a, float2 b) { return __ffma2_rn(
 __device__ __forceinline__ float2 mul2_(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// D2Q9 central moments -> populations (see central_to_pop9_), FP32
-template <bool REST_LAST>
-__device__ __forceinline__ void central_to_pop9_f_(const float dk[9], const float k[9], float ux, float uy, float g[9])
+// D2Q9 central moments -> populations (see central_to_pop9_), FP32.  SCALED: the results
+// come out multiplied by the storage scale so (FP16 storage), folded into the constants.
+template <bool REST_LAST, bool SCALED = false>
+__device__ __forceinline__ void central_to_pop9_f_(const float dk[9], const float k[9], float ux, float uy, float g[9],
+                                                   float so = 1.f)
 {
+    const float hs = SCALED ? 0.5f * so : 0.5f, qs = SCALED ? 0.25f * so : 0.25f;
     const float2 U = f2_(ux, uy), U2 = mul2_(U, U);
     const float ux2 = U2.x, uy2 = U2.y, uxy = ux * uy;
     const float r00 = dk[0];
@@ -229,45 +232,50 @@ __device__ __forceinline__ void central_to_pop9_f_(const float dk[9], const floa
     const float2 Q = f2_(r12, r21), W = f2_(r11, r22);
     const float2 E = sub2_(R2, bc2_(r22));   // r20 - r22, r02 - r22
     const float2 V = sub2_(R1, Q);            // r10 - r12, r01 - r21
-    const float2 G12 = mul2_(bc2_(0.5f), add2_(E, V));   // g1, g2
-    const float2 G34 = mul2_(bc2_(0.5f), sub2_(E, V));   // g3, g4
+    const float2 G12 = mul2_(bc2_(hs), add2_(E, V));   // g1, g2
+    const float2 G34 = mul2_(bc2_(hs), sub2_(E, V));   // g3, g4
     const float2 S = add2_(W, Q);                         // r11 + r12, r22 + r21
     const float2 D = sub2_(W, Q);                         // r11 - r12, r22 - r21
     g[1] = G12.x;
     g[2] = G12.y;
     g[3] = G34.x;
     g[4] = G34.y;
-    g[5] = 0.25f * (S.x + S.y);
-    g[6] = 0.25f * (S.y - S.x);
-    g[7] = 0.25f * (D.x + D.y);
-    g[8] = 0.25f * (D.y - D.x);
+    g[5] = qs * (S.x + S.y);
+    g[6] = qs * (S.y - S.x);
+    g[7] = qs * (D.x + D.y);
+    g[8] = qs * (D.y - D.x);
     if constexpr (REST_LAST) {
         const float2 P = add2_(G12, G34);
-        g[0] = r00 - ((P.x + P.y) + ((g[5] + g[6]) + (g[7] + g[8])));
+        const float rest = (P.x + P.y) + ((g[5] + g[6]) + (g[7] + g[8]));
+        g[0] = SCALED ? r00 * so - rest : r00 - rest;
     } else {
         g[0] = r00 - R2.x - R2.y + r22;
+        if constexpr (SCALED) g[0] *= so;
     }
 }
 
 // D2Q5 central moments -> populations (see central_to_pop5_), FP32: dk = (dk0, DK1, DK2),
-// k = (k0, K1, .) as pairs (first and second moments), U = (ux, uy), U2 = (ux^2, uy^2)
-template <bool REST_LAST>
+// k = (k0, K1, .) as pairs (first and second moments), U = (ux, uy), U2 = (ux^2, uy^2);
+// SCALED as for central_to_pop9_f_
+template <bool REST_LAST, bool SCALED = false>
 __device__ __forceinline__ void central_to_pop5_f_(float dk0, float2 DK1, float2 DK2, float k0, float2 K1, float2 U,
-                                                   float2 U2, float f[5])
+                                                   float2 U2, float f[5], float so = 1.f)
 {
+    const float hs = SCALED ? 0.5f * so : 0.5f;
     const float2 R1 = fma2_(U, bc2_(k0), DK1);                            // r10, r01
     const float2 R2 = fma2_(U2, bc2_(k0), fma2_(add2_(U, U), K1, DK2));   // r20, r02
-    const float2 A = mul2_(bc2_(0.5f), add2_(R1, R2));                    // f1, f2
-    const float2 B = mul2_(bc2_(0.5f), sub2_(R2, R1));                    // f3, f4
+    const float2 A = mul2_(bc2_(hs), add2_(R1, R2));                      // f1, f2
+    const float2 B = mul2_(bc2_(hs), sub2_(R2, R1));                      // f3, f4
     f[1] = A.x;
     f[2] = A.y;
     f[3] = B.x;
     f[4] = B.y;
     if constexpr (REST_LAST) {
         const float2 S = add2_(A, B);
-        f[0] = dk0 - (S.x + S.y);
+        f[0] = SCALED ? dk0 * so - (S.x + S.y) : dk0 - (S.x + S.y);
     } else {
         f[0] = dk0 - R2.x - R2.y;
+        if constexpr (SCALED) f[0] *= so;
     }
 }
 
@@ -282,11 +290,14 @@ __device__ __forceinline__ void central_to_pop5_f_(float dk0, float2 DK1, float2
 // (measured on a float32 conduction lattice: the T error after 2000 steps falls from
 // 2.9e-6 to 1.8e-7, the level of float32 storage alone); used for the conserved scalar
 // lattices (phi, T).
-template <typename Real, bool REST_LAST = false>
-__device__ __forceinline__ void central_to_pop9_(const Real dk[9], const Real k[9], Real ux, Real uy, Real g[9])
+// SCALED (FP32 arithmetic only): results multiplied by the storage scale so.
+template <typename Real, bool REST_LAST = false, bool SCALED = false>
+__device__ __forceinline__ void central_to_pop9_(const Real dk[9], const Real k[9], Real ux, Real uy, Real g[9],
+                                                 Real so = Real(1))
 {
+    static_assert(!SCALED || std::is_same<Real, float>::value, "storage scales go with FP32 arithmetic");
     if constexpr (std::is_same<Real, float>::value) {
-        central_to_pop9_f_<REST_LAST>(dk, k, ux, uy, g);
+        central_to_pop9_f_<REST_LAST, SCALED>(dk, k, ux, uy, g, so);
         return;
     }
     const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
@@ -316,13 +327,15 @@ __device__ __forceinline__ void central_to_pop9_(const Real dk[9], const Real k[
 }
 
 // D2Q5 analogue: basis 1, e_x, e_y, e_x^2, e_y^2 (the first five rows of F(-u)).
-template <typename Real, bool REST_LAST = false>
-__device__ __forceinline__ void central_to_pop5_(const Real dk[5], const Real k[5], Real ux, Real uy, Real f[5])
+template <typename Real, bool REST_LAST = false, bool SCALED = false>
+__device__ __forceinline__ void central_to_pop5_(const Real dk[5], const Real k[5], Real ux, Real uy, Real f[5],
+                                                 Real so = Real(1))
 {
+    static_assert(!SCALED || std::is_same<Real, float>::value, "storage scales go with FP32 arithmetic");
     if constexpr (std::is_same<Real, float>::value) {
         const float2 U = f2_(ux, uy);
-        central_to_pop5_f_<REST_LAST>(dk[0], f2_(dk[1], dk[2]), f2_(dk[3], dk[4]), k[0], f2_(k[1], k[2]), U,
-                                      mul2_(U, U), f);
+        central_to_pop5_f_<REST_LAST, SCALED>(dk[0], f2_(dk[1], dk[2]), f2_(dk[3], dk[4]), k[0], f2_(k[1], k[2]), U,
+                                              mul2_(U, U), f, so);
         return;
     }
     const Real r00 = dk[0];
@@ -360,9 +373,11 @@ __device__ __forceinline__ void raw_first_(const Real *p, Real &m10, Real &m01)
 // reference is even in x) the pre-collision first central moments are k10 = m10 - u_x phi
 // and k01 = m01 + Ry(y) - u_y phi; the reference's own post-collision first moments are
 // (0, t01(y)), t01 ~ M_phi theta0. ----
-template <int Q, typename Real>
+// (SCALED: s comes out multiplied by the storage scale so.)
+template <int Q, typename Real, bool SCALED = false>
 __device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, Real dphi, Real phi, Real ux, Real uy,
-                                                   Real nx, Real my, Real th0, Real dth, Real c01, Real M, Real om)
+                                                   Real nx, Real my, Real th0, Real dth, Real c01, Real M, Real om,
+                                                   Real so = Real(1))
 {
     if constexpr (std::is_same<Real, float>::value && Q == 5) {
         const float w1 = 1.f - om, oM = om * M, c2 = 1.f / 3.f;
@@ -371,7 +386,7 @@ __device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, 
         const float2 T = fma2_(bc2_(w1), fma2_(NU, bc2_(phi), f2_(m10, m01)),
                                f2_(oM * (th0 + dth) * nx, oM * (th0 * my + dth * (1.f + my)) + c01));
         const float2 T1 = add2_(T, f2_(0.f, M * th0));
-        central_to_pop5_f_<true>(dphi, T, bc2_(c2 * dphi), phi, T1, U, mul2_(U, U), s);
+        central_to_pop5_f_<true, SCALED>(dphi, T, bc2_(c2 * dphi), phi, T1, U, mul2_(U, U), s, so);
         return;
     }
     const Real w1 = Real(1) - om, oM = om * M;
@@ -382,11 +397,11 @@ __device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, 
     if constexpr (Q == 9) {
         const Real dk[9] = {dphi, t10, dt01, c2d, c2d, Real(0), Real(0), Real(0), dphi * Real(1.0 / 9.0)};
         const Real k[9] = {phi, t10, t01, c2p, c2p, Real(0), Real(0), Real(0), phi * Real(1.0 / 9.0)};
-        central_to_pop9_<Real, true>(dk, k, ux, uy, s);
+        central_to_pop9_<Real, true, SCALED>(dk, k, ux, uy, s, so);
     } else {
         const Real dk[5] = {dphi, t10, dt01, c2d, c2d};
         const Real k[5] = {phi, t10, t01, c2p, c2p};
-        central_to_pop5_<Real, true>(dk, k, ux, uy, s);
+        central_to_pop5_<Real, true, SCALED>(dk, k, ux, uy, s, so);
     }
 }
 
@@ -395,8 +410,9 @@ __device__ __forceinline__ void collide_phase_dev_(Real *s, Real m10, Real m01, 
 // are the Maxwellian central moments per unit T and Wc(u) those of the weights.  In: the
 // pulled populations' dT = T - T_ref and first raw moments (m10, m01); out: h = the
 // post-collision populations. ----
-template <int Q, typename Real>
-__device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Real dT, Real ux, Real uy, Real Tr, Real om)
+template <int Q, typename Real, bool SCALED = false>
+__device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Real dT, Real ux, Real uy, Real Tr, Real om,
+                                                Real so = Real(1))
 {
     if constexpr (std::is_same<Real, float>::value && Q == 5) {
         const float c2 = 1.f / 3.f;
@@ -404,7 +420,7 @@ __device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Rea
         const float2 K = fma2_(mul2_(bc2_(-1.f), U), bc2_(dT), f2_(m10, m01));          // k10, k01
         const float2 T = fma2_(bc2_(om), sub2_(mul2_(bc2_(Tr), U), K), K);               // t10, t01
         const float2 K2 = fma2_(bc2_(-Tr), U2, bc2_(c2 * dT));                           // k20, k02
-        central_to_pop5_f_<true>(dT, T, K2, dT, T, U, U2, h);
+        central_to_pop5_f_<true, SCALED>(dT, T, K2, dT, T, U, U2, h, so);
         return;
     }
     const Real k10 = m10 - ux * dT, k01 = m01 - uy * dT;
@@ -421,10 +437,10 @@ __device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Rea
                            Tr * (c2 + ux2) * uy,
                            Tr * (c2 + uy2) * ux,
                            Real(1.0 / 9.0) * dT - Tr * (c2 * (ux2 + uy2) + ux2 * uy2)};
-        central_to_pop9_<Real, true>(k, k, ux, uy, h);
+        central_to_pop9_<Real, true, SCALED>(k, k, ux, uy, h, so);
     } else {
         const Real k[5] = {dT, t10, t01, c2 * dT - Tr * ux2, c2 * dT - Tr * uy2};
-        central_to_pop5_<Real, true>(k, k, ux, uy, h);
+        central_to_pop5_<Real, true, SCALED>(k, k, ux, uy, h, so);
     }
 }
 
@@ -432,17 +448,25 @@ __device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Rea
 // and 11 relax at omega_nu (pre-collision values needed); every other central moment
 // is replaced by equilibrium + source / 2.  Deviation equilibrium:
 //   eta^eq - p0 Wc(u) = dp Wc(u) + rho c^2 D(u). ----
-template <typename Real>
+// (SCALED: g comes in and out multiplied by the storage scale, 1 / si and so; s0, sx, sy
+// are unscaled.)
+template <typename Real, bool SCALED = false>
 __device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real ux, Real uy, Real Fpx, Real Fpy,
-                                              Real Ftx, Real Fty, Real om, Real s0, Real sx, Real sy)
+                                              Real Ftx, Real Fty, Real om, Real s0, Real sx, Real sy,
+                                              Real si = Real(1), Real so = Real(1))
 {
+    static_assert(!SCALED || std::is_same<Real, float>::value, "storage scales go with FP32 arithmetic");
     if constexpr (std::is_same<Real, float>::value) {
         const float c2 = 1.f / 3.f, hf = 0.5f;
         const float2 U = f2_(ux, uy), U2 = mul2_(U, U), NU = mul2_(bc2_(-1.f), U);
         const float uxy = ux * uy;
         const float t5678 = (g[5] + g[6]) + (g[7] + g[8]);
-        const float2 R2 = add2_(add2_(f2_(g[1], g[2]), f2_(g[3], g[4])), bc2_(t5678));          // r20, r02
-        const float r11 = (g[5] - g[6]) + (g[7] - g[8]);
+        float2 R2 = add2_(add2_(f2_(g[1], g[2]), f2_(g[3], g[4])), bc2_(t5678));                // r20, r02
+        float r11 = (g[5] - g[6]) + (g[7] - g[8]);
+        if constexpr (SCALED) {
+            R2 = mul2_(bc2_(si), R2);
+            r11 *= si;
+        }
         const float2 E = fma2_(U2, bc2_(s0), fma2_(add2_(NU, NU), f2_(sx, sy), R2));          // e20, e02
         const float e11 = r11 - uy * sx - ux * sy + uxy * s0;
         const float2 A = add2_(bc2_(c2), U2);                                                  // ax, ay
@@ -471,7 +495,7 @@ __device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real u
         k[6] = q21;
         k[7] = q12;
         k[8] = q22;
-        central_to_pop9_f_<false>(k, k, ux, uy, g);
+        central_to_pop9_f_<false, SCALED>(k, k, ux, uy, g, so);
         return;
     }
     const Real c2 = Real(1.0 / 3.0), hf = Real(0.5);

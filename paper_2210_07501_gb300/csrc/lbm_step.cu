@@ -66,9 +66,11 @@ __device__ __forceinline__ void grad3_(const Real *rm, const Real *r0, const Rea
 //   KIND 0: phase field, specular reflection (free slip, no flux through the wall)
 //   KIND 1: flow, halfway bounce-back (no slip)
 //   KIND 2: energy, anti-bounce-back to the wall temperature where the link crosses the wall
+// Values come out in stored units (for FP16 storage: times its scale; wscale multiplies
+// the anti-bounce-back wall term accordingly).
 template <int KIND, int Q, typename Real, typename Store>
 __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int ny, int nx, int y, int x, int xm,
-                                          int xp, Real iscale, const Real *__restrict__ twall, Real dTcold, Real *out)
+                                          int xp, Real wscale, const Real *__restrict__ twall, Real dTcold, Real *out)
 {
     const int r0 = y * pitch;
 #pragma unroll
@@ -85,10 +87,11 @@ __device__ __forceinline__ void pull_row_(const Store *const *pl, int pitch, int
         } else {
             v = ld_<Real, Store>(pl[opp_(a)] + (r0 + x));
         }
-        if constexpr (scaled_<Store>()) v *= iscale;
         if (KIND == 2 && wall) {
             const Real tw = ey > 0 ? twall[(1 - ex) * nx + x] : dTcold;
-            v = -v + Real(2.0 * w_<Q>(a)) * tw;
+            Real t = Real(2.0 * w_<Q>(a)) * tw;
+            if constexpr (scaled_<Store>()) t *= wscale;
+            v = -v + t;
         }
         out[a] = v;
     }
@@ -184,13 +187,16 @@ __device__ __forceinline__ Real lds_(const Store *p)
     else return Real(*p);
 }
 
-// Columns per strip: 128.  FP32 and FP16 storage: five CTAs of 5 warps per SM (72 registers
-// per thread, a three-stage ring for FP32; measured 1 % faster than four CTAs with a
-// four-stage ring on the 8192 x 2048 channel, 11 % for FP16; 256 columns ran 2 % slower).
-// FP64 needs ~125-165 registers per thread: two CTAs per SM.
+// Columns per strip: 128.  FP32 storage: five CTAs of 5 warps per SM (72 registers per
+// thread, a three-stage ring; measured 1 % faster than four CTAs with a four-stage ring on
+// the 8192 x 2048 channel; 256 columns ran 2 % slower).  FP16 storage: six CTAs (64
+// registers; its stages are half the size).  FP64 needs ~125-165 registers per thread: two.
 template <typename Real> constexpr int march_width() { return 128; }
 // Resident CTAs per SM the kernels are built for (registers and shared memory).
-template <typename Real> constexpr int march_ctas() { return sizeof(Real) == 4 ? 5 : 2; }
+template <typename Real, typename Store> constexpr int march_ctas()
+{
+    return sizeof(Real) == 8 ? 2 : (sizeof(Store) == 2 ? 6 : 5);
+}
 // The many-channel kernel reads its arguments through a pointer and needs more registers:
 // at 72 it spilled and ran the 16-channel sweep 14 % slower than with four CTAs per SM.
 template <typename Real> constexpr int batch_ctas() { return sizeof(Real) == 4 ? 4 : 2; }
@@ -206,7 +212,7 @@ template <typename Real, typename Store, int QF, int QT, int TX> struct StageGeo
     static_assert(RXO % 16 == 0, "the staged reference values need a 16-byte aligned slot");
     static constexpr int RINGS = 8 * (TX + 4) * (int)sizeof(Real) + 16 * (TX + 2) * (int)sizeof(Real);
     // deepest ring that leaves room for march_ctas() CTAs per SM (228 KiB, 1 KiB reserved per CTA)
-    static constexpr int BUDGET = 233472 / march_ctas<Real>() - 1024 - 128 - 16 - RINGS;
+    static constexpr int BUDGET = 233472 / march_ctas<Real, Store>() - 1024 - 128 - 16 - RINGS;
     static constexpr int D = (4 * BYTES + 128 <= BUDGET) ? 4 : ((3 * BYTES + 128 <= BUDGET) ? 3 : 2);
     static constexpr int DYN = D * BYTES + 128;              // + one mbarrier per slot
 };
@@ -317,15 +323,16 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             else mbar_arrive_(&s_bar[sl]);
         }
     };
-    // Pulled values of a completed stage at the thread's columns (wall rules of Sec. 5.1).
+    // Pulled values of a completed stage at the thread's columns (wall rules of Sec. 5.1), in
+    // stored units: with FP16 storage the sums and moments formed from them are rescaled
+    // (put_phi_dr, put_sig, keep_f, keep_h, the flow's moments), not each value.
+    constexpr bool SCALED = scaled_<Store>();
     auto read_f = [&](int sl, Real *f) {
         const Store *st = stage_pop(sl) + HS + cf;
 #pragma unroll
         for (int a = 0; a < QF; ++a) {
             // specular reflection keeps the x shift of the link
-            Real v = lds_<Real, Store>(st + a * RS - ex_(a));
-            if constexpr (scaled_<Store>()) v *= A.isf;
-            f[a] = v;
+            f[a] = lds_<Real, Store>(st + a * RS - ex_(a));
         }
     };
     // WALLS = false: rows away from the walls (no link of this row crosses one)
@@ -339,8 +346,11 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const int ex = ex_(a), ey = ey_(a);
             const bool wall = (ey > 0 && wb) || (ey < 0 && wt);
             Real v = lds_<Real, Store>(st + a * RS - (wall ? 0 : ex));
-            if constexpr (scaled_<Store>()) v *= A.ish;
-            if (wall) v = -v + Real(2.0 * w_<QT>(a)) * (ey > 0 ? A.twall[(1 - ex) * nx + xh] : P.dTcold);
+            if (wall) {
+                Real t = Real(2.0 * w_<QT>(a)) * (ey > 0 ? A.twall[(1 - ex) * nx + xh] : P.dTcold);
+                if constexpr (SCALED) t *= A.sh;
+                v = -v + t;
+            }
             h[a] = v;
         }
         dp = stage_dp(sl)[HD + ch];
@@ -353,18 +363,16 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         for (int a = 0; a < 9; ++a) {
             const int ey = ey_(a);
             const bool wall = (ey > 0 && wb) || (ey < 0 && wt);
-            Real v = lds_<Real, Store>(st + a * RS - (wall ? 0 : ex_(a)));
-            if constexpr (scaled_<Store>()) v *= A.isg;
-            g[a] = v;
+            g[a] = lds_<Real, Store>(st + a * RS - (wall ? 0 : ex_(a)));
         }
     };
     // Direct loads (first rows of a segment only).
     auto load_f = [&](int r, Real *f) {
-        pull_row_<0, QF>(A.fi, pitch, ny, nx, mirror_row_(r, ny), xf, xfm, xfp, A.isf, A.twall, P.dTcold, f);
+        pull_row_<0, QF>(A.fi, pitch, ny, nx, mirror_row_(r, ny), xf, xfm, xfp, A.sf, A.twall, P.dTcold, f);
     };
     auto load_h = [&](int r, Real *h, Real &dp) {
         const int gy = mirror_row_(r, ny);
-        pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, xh, xhm, xhp, A.ish, A.twall, P.dTcold, h);
+        pull_row_<2, QT>(A.hi, pitch, ny, nx, gy, xh, xhm, xhp, A.sh, A.twall, P.dTcold, h);
         dp = A.dp_in[gy * pitch + xh];
     };
     // phi - phi0 of row r (ghost rows: of the mirrored row) from the pulled deviations and
@@ -373,6 +381,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         Real dphi = f[0];
 #pragma unroll
         for (int a = 1; a < QF; ++a) dphi += f[a];
+        if constexpr (SCALED) dphi *= A.isf;
         if constexpr (std::is_same<Real, double>::value) dphi += dr;
         else dphi = (dphi + drlo) + dr;
         s_phi[r & 7][cf + 2] = dphi;
@@ -386,6 +395,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
         Real dT = h[0];
 #pragma unroll
         for (int a = 1; a < QT; ++a) dT += h[a];
+        if constexpr (SCALED) dT *= A.ish;
         Real dTs = dT;
         if (r == -1) dTs = Real(2) * A.twall[nx + xh] - dT;   // T_ghost = 2 T_w - T_adjacent
         else if (r == ny) dTs = Real(2) * P.dTcold - dT;
@@ -397,10 +407,14 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
     };
     // what the collisions keep of pulled populations: first raw moments of f, and
     // (T - T_ref, first raw moments) of h
-    auto keep_f = [&](const Real *f, Real *m) { raw_first_<QF>(f, m[0], m[1]); };
+    auto keep_f = [&](const Real *f, Real *m) {
+        raw_first_<QF>(f, m[0], m[1]);
+        if constexpr (SCALED) m[0] *= A.isf, m[1] *= A.isf;
+    };
     auto keep_h = [&](const Real *h, Real dT, Real *m) {
         m[0] = dT;
         raw_first_<QT>(h, m[1], m[2]);
+        if constexpr (SCALED) m[1] *= A.ish, m[2] *= A.ish;
     };
     // grad phi = grad (phi - phi0) + (0, d_y phi0); the normal as (n_x, n_y - 1)
     auto put_n_g = [&](int r, Real gref) {
@@ -557,9 +571,10 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real Fpx = -dpx + c2 * P.drho * gpx, Fpy = -dpy + c2 * P.drho * gpy;
             const Real rho = P.rhoA + phi * P.drho;
             const Real irho = rcp_(rho);
-            const Real s0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-            const Real sx = (g[1] - g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
-            const Real sy = (g[2] - g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
+            Real s0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+            Real sx = (g[1] - g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
+            Real sy = (g[2] - g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
+            if constexpr (SCALED) s0 *= A.isg, sx *= A.isg, sy *= A.isg;
             const Real irc2 = Real(3) * irho;
             const Real ux = (sx + hf * c2 * Ftx) * irc2;
             const Real uy = (sy + hf * c2 * Fty) * irc2;
@@ -569,10 +584,11 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             // theta(phi) - theta(phi0) = (4 / W) dphi (1 - 2 phi0 - dphi)
             const Real dth = P.W4 * dphi * (Real(1) - Real(2) * phi_ref - dphi);
             Real fo[QF], ho[QT];
-            collide_phase_dev_<QF>(fo, fm0[0], fm0[1], dphi, phi, ux, uy, nxv, nC.y, th0, dth, c01, P.Mphi,
-                                   P.omega_phi);
-            collide_flow_(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy);
-            collide_energy_<QT>(ho, hm0[1], hm0[2], dT, ux, uy, P.T_ref, om_T);
+            // (FP16 storage: the results come out in stored units)
+            collide_phase_dev_<QF, Real, SCALED>(fo, fm0[0], fm0[1], dphi, phi, ux, uy, nxv, nC.y, th0, dth, c01,
+                                                 P.Mphi, P.omega_phi, A.sf);
+            collide_flow_<Real, SCALED>(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy, A.isg, A.sg);
+            collide_energy_<QT, Real, SCALED>(ho, hm0[1], hm0[2], dT, ux, uy, P.T_ref, om_T, A.sh);
             const int o = y * pitch + x;
             // one unsigned 32-bit byte offset from every plane's base (measured 2 % faster than
             // plane base + element index)
@@ -580,21 +596,15 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             auto at = [&](Store *base) { return reinterpret_cast<Store *>(reinterpret_cast<char *>(base) + ob); };
 #pragma unroll
             for (int a = 0; a < QF; ++a) {
-                Real v = fo[a];
-                if constexpr (scaled_<Store>()) v *= A.sf;
-                st_(at(A.fo[a]), v);
+                st_(at(A.fo[a]), fo[a]);
             }
 #pragma unroll
             for (int a = 0; a < 9; ++a) {
-                Real v = g[a];
-                if constexpr (scaled_<Store>()) v *= A.sg;
-                st_(at(A.go[a]), v);
+                st_(at(A.go[a]), g[a]);
             }
 #pragma unroll
             for (int a = 0; a < QT; ++a) {
-                Real v = ho[a];
-                if constexpr (scaled_<Store>()) v *= A.sh;
-                st_(at(A.ho[a]), v);
+                st_(at(A.ho[a]), ho[a]);
             }
             A.dp_out[o] = dp;
             if (A.macro) {
@@ -618,7 +628,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
 }
 
 template <typename Real, typename Store, int QF, int QT, int TX>
-__global__ void __launch_bounds__(TX + 32, march_ctas<Real>()) march_kernel(const StepArgs<Real, Store> A, int seg)
+__global__ void __launch_bounds__(TX + 32, march_ctas<Real, Store>()) march_kernel(const StepArgs<Real, Store> A, int seg)
 {
     march_body<Real, Store, QF, QT, TX>(A, seg, blockIdx.x, blockIdx.y);
 }
