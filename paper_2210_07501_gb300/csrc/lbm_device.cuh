@@ -444,29 +444,52 @@ __device__ __forceinline__ void collide_energy_(Real *h, Real m10, Real m01, Rea
     }
 }
 
+// ---- Raw moments of the pulled flow populations that the flow step needs: the zeroth and
+// first (s0, sx, sy, which give p and u, Sec. 4.2) and the second (r20, r02, r11, the F(u)
+// rows of the pre-collision central moments 20, 02, 11).  FP32: from the packed sums and
+// differences of (g1, g2) and (g3, g4), (g5, g7) and (g6, g8). ----
+template <typename Real>
+__device__ __forceinline__ void flow_raw_moments_(const Real *g, Real &s0, Real &sx, Real &sy, Real &r20, Real &r02,
+                                                  Real &r11)
+{
+    if constexpr (std::is_same<Real, float>::value) {
+        const float2 G12 = f2_(g[1], g[2]), G34 = f2_(g[3], g[4]), G57 = f2_(g[5], g[7]), G68 = f2_(g[6], g[8]);
+        const float2 A = add2_(G12, G34), B = sub2_(G12, G34);   // g1 +- g3, g2 +- g4
+        const float2 C = add2_(G57, G68), E = sub2_(G57, G68);   // g5 +- g6, g7 +- g8
+        const float t = C.x + C.y;
+        s0 = (g[0] + (A.x + A.y)) + t;
+        sx = B.x + (E.x - E.y);
+        sy = B.y + (C.x - C.y);
+        r20 = A.x + t;
+        r02 = A.y + t;
+        r11 = E.x + E.y;
+    } else {
+        s0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+        sx = (g[1] - g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
+        sy = (g[2] - g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
+        r20 = (g[1] + g[3]) + ((g[5] + g[6]) + (g[7] + g[8]));
+        r02 = (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8]));
+        r11 = (g[5] - g[6]) + (g[7] - g[8]);
+    }
+}
+
 // ---- Sec. 4.2 two-fluid collision on g - w p0.  Only the trace-free second moment 2d
 // and 11 relax at omega_nu (pre-collision values needed); every other central moment
 // is replaced by equilibrium + source / 2.  Deviation equilibrium:
-//   eta^eq - p0 Wc(u) = dp Wc(u) + rho c^2 D(u). ----
-// (SCALED: g comes in and out multiplied by the storage scale, 1 / si and so; s0, sx, sy
-// are unscaled.)
+//   eta^eq - p0 Wc(u) = dp Wc(u) + rho c^2 D(u).  In: the pulled populations' raw moments
+// (flow_raw_moments_); out: g = the post-collision populations (SCALED: multiplied by the
+// storage scale so). ----
 template <typename Real, bool SCALED = false>
 __device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real ux, Real uy, Real Fpx, Real Fpy,
-                                              Real Ftx, Real Fty, Real om, Real s0, Real sx, Real sy,
-                                              Real si = Real(1), Real so = Real(1))
+                                              Real Ftx, Real Fty, Real om, Real s0, Real sx, Real sy, Real r20,
+                                              Real r02, Real r11, Real so = Real(1))
 {
     static_assert(!SCALED || std::is_same<Real, float>::value, "storage scales go with FP32 arithmetic");
     if constexpr (std::is_same<Real, float>::value) {
         const float c2 = 1.f / 3.f, hf = 0.5f;
         const float2 U = f2_(ux, uy), U2 = mul2_(U, U), NU = mul2_(bc2_(-1.f), U);
         const float uxy = ux * uy;
-        const float t5678 = (g[5] + g[6]) + (g[7] + g[8]);
-        float2 R2 = add2_(add2_(f2_(g[1], g[2]), f2_(g[3], g[4])), bc2_(t5678));                // r20, r02
-        float r11 = (g[5] - g[6]) + (g[7] - g[8]);
-        if constexpr (SCALED) {
-            R2 = mul2_(bc2_(si), R2);
-            r11 *= si;
-        }
+        const float2 R2 = f2_(r20, r02);
         const float2 E = fma2_(U2, bc2_(s0), fma2_(add2_(NU, NU), f2_(sx, sy), R2));          // e20, e02
         const float e11 = r11 - uy * sx - ux * sy + uxy * s0;
         const float2 A = add2_(bc2_(c2), U2);                                                  // ax, ay
@@ -501,9 +524,6 @@ __device__ __forceinline__ void collide_flow_(Real *g, Real rho, Real dp, Real u
     const Real c2 = Real(1.0 / 3.0), hf = Real(0.5);
     const Real ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     // pre-collision central moments 20, 02, 11 (F(u) rows on the raw moments)
-    const Real r20 = (g[1] + g[3]) + ((g[5] + g[6]) + (g[7] + g[8]));
-    const Real r02 = (g[2] + g[4]) + ((g[5] + g[6]) + (g[7] + g[8]));
-    const Real r11 = (g[5] - g[6]) + (g[7] - g[8]);
     const Real e20 = r20 - Real(2) * ux * sx + ux2 * s0;
     const Real e02 = r02 - Real(2) * uy * sy + uy2 * s0;
     const Real e11 = r11 - uy * sx - ux * sy + uxy * s0;

@@ -55,6 +55,16 @@ template <typename Real>
 __device__ __forceinline__ void grad3_(const Real *rm, const Real *r0, const Real *rp, int c, Real &gx, Real &gy)
 {
     const Real c1 = Real(1.0 / 3.0), c2 = Real(1.0 / 12.0);
+    if constexpr (std::is_same<Real, float>::value) {
+        // diagonal terms from (NE, NW) +- (SE, SW): (NE + SE) - (NW + SW) and
+        // (NE - SE) + (NW - SW), both halves of a pair in one packed instruction
+        const float2 P = f2_(rp[c + 1], rp[c - 1]), Q = f2_(rm[c + 1], rm[c - 1]);
+        const float2 S = add2_(P, Q), D = sub2_(P, Q);
+        const float2 G = fma2_(bc2_(c1), f2_(r0[c + 1] - r0[c - 1], rp[c] - rm[c]),
+                               mul2_(bc2_(c2), f2_(S.x - S.y, D.x + D.y)));
+        gx = G.x, gy = G.y;
+        return;
+    }
     const Real ne = rp[c + 1], nw = rp[c - 1], se = rm[c + 1], sw = rm[c - 1];
     gx = c1 * (r0[c + 1] - r0[c - 1]) + c2 * ((ne - nw) + (se - sw));
     gy = c1 * (rp[c] - rm[c]) + c2 * ((ne - se) + (nw - sw));
@@ -571,10 +581,9 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             const Real Fpx = -dpx + c2 * P.drho * gpx, Fpy = -dpy + c2 * P.drho * gpy;
             const Real rho = P.rhoA + phi * P.drho;
             const Real irho = rcp_(rho);
-            Real s0 = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-            Real sx = (g[1] - g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
-            Real sy = (g[2] - g[4]) + ((g[5] + g[6]) - (g[7] + g[8]));
-            if constexpr (SCALED) s0 *= A.isg, sx *= A.isg, sy *= A.isg;
+            Real s0, sx, sy, r20, r02, r11;
+            flow_raw_moments_(g, s0, sx, sy, r20, r02, r11);
+            if constexpr (SCALED) s0 *= A.isg, sx *= A.isg, sy *= A.isg, r20 *= A.isg, r02 *= A.isg, r11 *= A.isg;
             const Real irc2 = Real(3) * irho;
             const Real ux = (sx + hf * c2 * Ftx) * irc2;
             const Real uy = (sy + hf * c2 * Fty) * irc2;
@@ -587,7 +596,7 @@ __device__ __forceinline__ void march_body(const StepArgs<Real, Store> &A, int s
             // (FP16 storage: the results come out in stored units)
             collide_phase_dev_<QF, Real, SCALED>(fo, fm0[0], fm0[1], dphi, phi, ux, uy, nxv, nC.y, th0, dth, c01,
                                                  P.Mphi, P.omega_phi, A.sf);
-            collide_flow_<Real, SCALED>(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy, A.isg, A.sg);
+            collide_flow_<Real, SCALED>(g, rho, dp, ux, uy, Fpx, Fpy, Ftx, Fty, om_nu, s0, sx, sy, r20, r02, r11, A.sg);
             collide_energy_<QT, Real, SCALED>(ho, hm0[1], hm0[2], dT, ux, uy, P.T_ref, om_T, A.sh);
             const int o = y * pitch + x;
             // one unsigned 32-bit byte offset from every plane's base (measured 2 % faster than
