@@ -31,7 +31,7 @@ def small_sweep(n=7, seed=5):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
 def test_batch_equals_single_handles(pkg, precision):
     ws = small_sweep()
     b = pkg.LbmBatch(ws, precision=precision)
