@@ -133,8 +133,10 @@ def test_steady_state_fp32_to_1e8():
     r <= 1e-8, residual checks every 1000 steps, from the closed-form temperature with the
     fluid at rest; residual history and the steady interface velocity and temperature
     against the closed form.  Default: 600,000 steps (the history and the comparison at
-    that point); LBM_STEADY_FULL=1: up to 4M steps or r <= 1e-8 (prints one JSON line);
-    LBM_STEADY_PRECISION=fp64 runs the FP64 path instead."""
+    that point); LBM_STEADY_FULL=1: up to 4M steps (LBM_STEADY_MAX) or r <= 1e-8 (prints
+    one JSON line); LBM_STEADY_K sets the steps between residual checks (r is per step, so a
+    longer interval divides the round-off part of r, not its decay); LBM_STEADY_PRECISION=fp64
+    runs the FP64 path instead."""
     import json
     import time
     from paper_2210_07501_gb300 import Lbm
@@ -142,11 +144,12 @@ def test_steady_state_fp32_to_1e8():
     precision = os.environ.get("LBM_STEADY_PRECISION", "fp32")
     w = case(2e-5)
     g = Lbm(w["domain"], w["params"], precision=precision)
-    g.lbm_set_check_interval(1000)
+    K = int(os.environ.get("LBM_STEADY_K", "1000"))
+    g.lbm_set_check_interval(K)
     g.lbm_init_fields(T=closed_form_T(w))
     g.lbm_autotune(3)
     hist, done, t0, ok = [], 0, time.perf_counter(), False
-    nmax, chunk = (4000000, 100000) if full else (600000, 100000)
+    nmax, chunk = (int(os.environ.get("LBM_STEADY_MAX", "4000000")), 100000) if full else (600000, 100000)
     while done < nmax and not ok:
         ok, n = g.lbm_run_to_steady(1e-8, min(chunk, nmax - done))
         done += n
@@ -155,7 +158,7 @@ def test_steady_state_fp32_to_1e8():
     f = g.lbm_fields()
     g.close()
     cmp = against_closed_form(w, f)
-    print(json.dumps({"steady": {"precision": precision, "converged": bool(ok), "steps": done, "seconds": secs,
+    print(json.dumps({"steady": {"precision": precision, "K": K, "converged": bool(ok), "steps": done, "seconds": secs,
                                  "history": hist, "closed_form": cmp}}))
     # the residual keeps falling: by more than 5x between 100k and 600k steps (measured
     # 1.07e-6 -> 8.5e-8 with checks every 100 steps)
